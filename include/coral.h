@@ -1,0 +1,209 @@
+/*
+ * coral.h — C ABI of the GB300 (sm_103a) substrate-step library.
+ *
+ * The library steps the toroidal substrate of Coralai (Barbieux & Canaan, arXiv 2406.09654):
+ * every cell senses a rotation-ordered 3x3 Moore neighbourhood (the "Kernel") of six sensor
+ * channels, runs the dense network selected by its GenomeIndex (weights generated by the
+ * genome's CPPN, HyperNEAT), and the physics turns the ten actuator outputs into the next
+ * substrate (Section "System Design", Section "Experiment", Fig. 1).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns a coral_status (0 = OK, negative = error). No C++ exception crosses
+ *    the ABI. After an error, coral_last_error(s) returns a message (valid until the next call
+ *    on the same substrate from the same thread).
+ *  - The library owns all device memory of a substrate; it allocates it in
+ *    coral_substrate_create and frees it in coral_substrate_destroy. Caller buffers are never
+ *    retained or freed by the library: they are copied in or out during the call (calls that
+ *    read host buffers wait for their copies; device-to-device copies are stream-ordered).
+ *  - Work is enqueued on the CUDA stream given at creation (NULL = the legacy default stream).
+ *    coral_step returns after enqueueing; errors that happen on the device (e.g. genome
+ *    capacity exhaustion) are latched in a device status word and returned by the next
+ *    synchronising call (coral_sync, coral_read_*).
+ *  - Grid layout: cell j = y * width + x, row y = 0 is "north"; the torus wraps in x and y.
+ *    Channel planes are float32 row-major [height][width]; C is [4][height][width].
+ *  - `*_on_device` flags: nonzero = the pointer is a CUDA device pointer on the substrate's
+ *    device (for example a torch tensor's data_ptr()), zero = host memory (pinned or pageable).
+ */
+#ifndef CORAL_H
+#define CORAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct coral_substrate coral_substrate;   /* opaque */
+
+typedef enum {
+  CORAL_OK = 0,
+  CORAL_E_INVALID = -1,   /* bad argument (NULL pointer, size out of range, bad params) */
+  CORAL_E_OOM = -2,       /* device allocation failed */
+  CORAL_E_CUDA = -3,      /* a CUDA runtime call or kernel launch failed */
+  CORAL_E_CAPACITY = -4,  /* a buffer given by the caller is too small */
+  CORAL_E_TIMEOUT = -5,   /* a bounded device-side wait gave up */
+  CORAL_E_STATE = -6      /* call out of order (e.g. step before any genome table load) */
+} coral_status;
+
+typedef enum {
+  CORAL_NET_FP32_PERCELL = 0,  /* plain FP32 CUDA-core network, one thread per cell */
+  CORAL_NET_BF16_GROUPED = 1   /* BF16 tcgen05 tensor-core network grouped by genome per tile,
+                                  FP32 TMEM accumulation, FP32 state */
+} coral_path;
+
+/* Channel bits for coral_read_channels / coral_state_load masks. */
+enum {
+  CORAL_CH_E = 1u << 0, CORAL_CH_I = 1u << 1,
+  CORAL_CH_C0 = 1u << 2, CORAL_CH_C1 = 1u << 3, CORAL_CH_C2 = 1u << 4, CORAL_CH_C3 = 1u << 5,
+  CORAL_CH_G = 1u << 6,   /* int32 GenomeIndex plane */
+  CORAL_CH_R = 1u << 7,   /* uint8 rotation plane, values 0=N 1=E 2=S 3=W */
+  CORAL_CH_ALL = 0xFFu
+};
+
+/*
+ * Method constants. The paper names these mechanisms but prints no values; the defaults
+ * returned by coral_params_default are the readings the library and its tests use.
+ */
+typedef struct coral_params {
+  int32_t hidden;          /* H: 0 = one layer 54->10; else 54->H->10 with H in {16,32,48,64} */
+  int32_t path;            /* coral_path */
+  float k_inv;             /* invest rate: i = k_inv * max(a4, 0)            (default 0.1) */
+  float k_liq;             /* liquidate rate: l = k_liq * max(a5, 0)         (default 0.1) */
+  float k_exp;             /* explore amount x = k_exp * m * I1              (default 0.5) */
+  float k_flow;            /* fraction of energy a cell sends along infrastructure (0.2) */
+  float e_day;             /* energy added per cell per step by day          (0.005) */
+  float e_night;           /* fraction of energy removed per step by night   (0.005) */
+  int32_t day_period;      /* day/night period T in steps; day = first half  (200) */
+  int32_t rotation;        /* 1 = kernel ordered by each cell's rotation, 0 = always north */
+  int32_t radiation_every; /* M: radiation after step t when (t+1) % M == 0; 0 = off */
+  uint32_t thr_mut;        /* mutation hit iff Philox word < thr_mut  (floor(p * 2^32)) */
+  uint32_t thr_merge;      /* merge hit iff Philox word < thr_merge */
+  float sigma_mut;         /* std of the Gaussian added to every gene by a mutation (0.05) */
+  uint32_t world;          /* Philox counter word 3 (distinguishes independent worlds) */
+  uint64_t seed;           /* Philox key */
+  int32_t fma_cutoff;      /* BF16 path: a genome with fewer cells than this in a 128-cell
+                              tile runs on the warp FMA path instead of the tensor cores */
+  int32_t max_mma_genomes; /* BF16 path: at most this many genomes per tile use tcgen05 */
+} coral_params;
+
+/* Per-step record kept in a device ring (read with coral_read_stats). */
+typedef struct coral_stats {
+  int64_t step;            /* step index t this record describes (state after step t) */
+  double sum_E;            /* FP64 total energy after the step */
+  double sum_I;            /* FP64 total infrastructure */
+  double sum_C[4];         /* FP64 totals of the communication channels */
+  int64_t n_explore;       /* cells that explored */
+  int64_t n_takeover;      /* cells taken over */
+  int64_t n_live;          /* live genome slots after radiation (-1 when no radiation ran) */
+  int64_t n_mut;           /* radiation: mutation hits */
+  int64_t n_merge;         /* radiation: merge hits with a different partner genome */
+  int64_t n_born;          /* radiation: children given a slot */
+  int64_t n_skipped;       /* radiation: hits dropped because no slot was free */
+} coral_stats;
+
+/* Fills *p with the default constants above (hidden = 0, FP32 path, seed 0). */
+int coral_params_default(coral_params* p);
+
+/*
+ * Creates a width x height torus with room for genome_capacity genome slots on the current
+ * CUDA device. Substrate: Section "System Design" (a tensor with width, height and named
+ * channels). width, height >= 3 (a 2-wide torus makes the north and south neighbours the
+ * same cell) and width * height < 2^31; genome_capacity in [1, 2^24].
+ * cuda_stream: a cudaStream_t (NULL = legacy default stream). Errors: E_INVALID, E_OOM, E_CUDA.
+ */
+int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
+                           int32_t genome_capacity, void* cuda_stream, coral_substrate** out);
+
+/* Frees every device buffer of s (synchronises its stream first). NULL is a no-op. */
+int coral_substrate_destroy(coral_substrate* s);
+
+/*
+ * Copies a full state in: E, I [N], C [4][N] float32; G [N] int32 (each in
+ * [0, genome_capacity)); R [N] uint8 (each in 0..3). Any of the five pointers may be NULL
+ * to leave that channel unchanged. Values of G and R are checked on the device; a bad
+ * value is reported by the next synchronising call as E_INVALID. Also resets the step
+ * counter to 0 unless coral_set_step is called afterwards.
+ */
+int coral_state_load(coral_substrate* s, const float* E, const float* I, const float* C,
+                     const int32_t* G, const uint8_t* R, int src_on_device);
+
+/*
+ * Genome table (Section "System Design": GenomeIndex locates the network parameters).
+ * Loads n genomes into slots 0..n-1 and marks slots n..capacity-1 free.
+ * cppn_genes: [n][18] float32 CPPN genes, or NULL for direct nets (then radiation must be
+ *   off). Gene layout: w[k][i] for hidden node k in (sin, gauss, tanh) and input i in
+ *   (x1, y1, x2, y2, bias), k-major (15 floats), then v[k], hidden->output (3 floats).
+ * dense_or_null: [n][net_floats] float32 direct nets, used when cppn_genes is NULL:
+ *   hidden = 0: W[10][54] row-major then b[10];
+ *   hidden = H: W1[H][54], b1[H], W2[10][H], b2[10].
+ * Input index i of W/W1 is 6 * rank + channel (rank 0 = centre, then the kernel order;
+ * channel order E, I, C0, C1, C2, C3); output order com0..3, invest, liquidate, explore0..3.
+ * With CPPN genes, call coral_cppn_generate_weights afterwards.
+ */
+int coral_genome_table_load(coral_substrate* s, int32_t n, const float* cppn_genes,
+                            const float* dense_or_null, int src_on_device);
+
+/*
+ * HyperNEAT (Section "System Design"; Fig. 1 C): queries each listed slot's CPPN at every
+ * connection (x1, y1, x2, y2) of its dense net and writes the FP32 net and its BF16
+ * tensor-core copy. Inputs sit at y = -1, hidden nodes at y = 0, outputs at y = +1, the n
+ * nodes of a layer at x = -1 + 2i/(n-1); biases are queried at (0, 0, x2, y2); weights are
+ * scaled by 1/sqrt(fan_in). slots_or_null: host int32 slot ids, or NULL = slots 0..n-1.
+ */
+int coral_cppn_generate_weights(coral_substrate* s, const int32_t* slots_or_null, int32_t n);
+
+/*
+ * Enqueues n_steps synchronous updates (Section "System Design": in discrete time steps each
+ * cell is updated) on the stream, each: sense + network + actuators (pass 1), exploration,
+ * energy flow and day/night (pass 2), FP64 totals into the stats ring, and radiation with
+ * CPPN regeneration after steps with (t+1) % M == 0 (Fig. 1 C). Returns after enqueueing.
+ * Errors: E_STATE before a genome table is loaded; E_CUDA on launch failure.
+ */
+int coral_step(coral_substrate* s, int32_t n_steps);
+
+/*
+ * Copies the planes selected by channel_mask (CORAL_CH_*) of the current state into dst,
+ * packed plane after plane in increasing bit order: E, I, C0..C3 as float32 [N], G as int32
+ * [N], R as uint8 [N]. dst_bytes must cover them all (else E_CAPACITY). Synchronises.
+ */
+int coral_read_channels(coral_substrate* s, uint32_t channel_mask, void* dst, size_t dst_bytes,
+                        int dst_on_device);
+
+/* Copies up to n stats records starting at step step_from (steps older than the ring's
+ * 4096-step window are gone: E_INVALID). Host memory. Synchronises. */
+int coral_read_stats(coral_substrate* s, int64_t step_from, int32_t n, coral_stats* out);
+
+/*
+ * Bucketing of cells by GenomeIndex: a stable counting sort of the current G (implemented
+ * as least-significant-digit passes of stable 8-bit counting sorts). dst_counts:
+ * [capacity] int32 cells per slot; dst_perm: [N] int32 cell ids, slot 0's cells in
+ * increasing order, then slot 1's, ... Either may be NULL. Host memory. Synchronises.
+ */
+int coral_read_perm(coral_substrate* s, int32_t* dst_counts, int32_t* dst_perm);
+
+/* Reads the genome table: genes [capacity][18] float32, parent [capacity] int32 (-1 for
+ * loaded genomes and never-used slots). Either may be NULL. Host memory. Synchronises. */
+int coral_read_genomes(coral_substrate* s, float* genes, int32_t* parent);
+
+/* Reads slot's FP32 dense net in the dense_or_null layout of coral_genome_table_load. */
+int coral_read_weights(coral_substrate* s, int32_t slot, float* dst, size_t dst_floats);
+
+/* Step index of the next coral_step (for checkpoint/resume; Philox is keyed by it). */
+int coral_set_step(coral_substrate* s, int64_t t);
+int coral_get_step(const coral_substrate* s, int64_t* t);
+
+/* Waits for the stream and returns the first latched device-side error, if any. */
+int coral_sync(coral_substrate* s);
+
+/* Message for the last error on s (or a generic one when s is NULL). Never NULL. */
+const char* coral_last_error(const coral_substrate* s);
+
+/* Floats in one dense net for a given hidden size (the dense_or_null row length). */
+int32_t coral_net_floats(int32_t hidden);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORAL_H */

@@ -1,0 +1,470 @@
+// C ABI of the substrate-step library: substrate lifetime, device memory ownership, loads and
+// reads, and the per-step launch sequence. Declarations and contracts: include/coral.h.
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <vector>
+
+#include "coral_internal.cuh"
+
+using namespace coral;
+
+struct coral_substrate {
+  coral_params p;
+  int W = 0, H = 0;
+  long long N = 0;
+  int cap = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sms = 0;
+  std::vector<void*> allocs;
+  Planes st[2] = {};
+  int cur = 0;
+  Pass1Bufs p1 = {};
+  GenomeArgs g = {};
+  bool genomes_loaded = false;
+  bool has_cppn = false;
+  Partial* part1 = nullptr;
+  Partial* part2 = nullptr;
+  coral_stats* ring = nullptr;
+  int* status = nullptr;
+  // radiation scratch
+  int32_t* count = nullptr;
+  int32_t* blockcnt = nullptr;
+  int32_t* blockoff = nullptr;
+  int4* hits = nullptr;
+  uint32_t* hitbits = nullptr;
+  int32_t* freelist = nullptr;
+  int32_t* newslots = nullptr;
+  int* counters = nullptr;
+  // bucketing scratch (allocated at the first coral_read_perm)
+  int32_t* sort_buf = nullptr;
+  long long t = 0;
+  int grid1 = 0, grid2 = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+int fail(coral_substrate* s, int code, const std::string& msg) {
+  if (s) s->err = msg;
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(coral_substrate* s, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(s, e == cudaErrorMemoryAllocation ? CORAL_E_OOM : CORAL_E_CUDA, m);
+}
+
+#define CK(s, call)                                        \
+  do {                                                     \
+    cudaError_t e_ = (call);                               \
+    if (e_ != cudaSuccess) return cuda_fail((s), e_, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(coral_substrate* s, T** p, size_t count) {
+  void* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, count * sizeof(T) + 256);
+  if (e != cudaSuccess) return e;
+  s->allocs.push_back(d);
+  *p = reinterpret_cast<T*>(d);
+  return cudaSuccess;
+}
+
+void free_all(coral_substrate* s) {
+  for (void* d : s->allocs) cudaFree(d);
+  s->allocs.clear();
+}
+
+bool valid_hidden(int h) { return h == 0 || h == 16 || h == 32 || h == 48 || h == 64; }
+
+StepArgs step_args(const coral_substrate* s) {
+  StepArgs a = {};
+  a.W = s->W;
+  a.H = s->H;
+  a.N = s->N;
+  a.hidden = s->p.hidden;
+  a.rotation = s->p.rotation;
+  a.k_inv = s->p.k_inv;
+  a.k_liq = s->p.k_liq;
+  a.k_exp = s->p.k_exp;
+  a.k_flow = s->p.k_flow;
+  a.is_day = ((s->t % s->p.day_period) * 2 < s->p.day_period) ? 1 : 0;
+  a.e_day = s->p.e_day;
+  a.e_night = s->p.e_night;
+  a.cur = s->st[s->cur];
+  a.nxt = s->st[s->cur ^ 1];
+  a.p1 = s->p1;
+  a.nets32 = s->g.nets32;
+  a.net_stride = s->g.net_stride;
+  a.nets16 = s->g.nets16;
+  a.blob_bytes = s->g.blob_bytes;
+  a.part1 = s->part1;
+  a.part2 = s->part2;
+  a.fma_cutoff = s->p.fma_cutoff;
+  a.max_mma_genomes = s->p.max_mma_genomes;
+  a.status = s->status;
+  return a;
+}
+
+cudaMemcpyKind kind_in(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
+cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
+
+int check_status(coral_substrate* s) {
+  int st = 0;
+  CK(s, cudaStreamSynchronize(s->stream));
+  CK(s, cudaMemcpy(&st, s->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) {
+    CK(s, cudaMemset(s->status, 0, sizeof(int)));
+    return fail(s, st, st == CORAL_E_INVALID ? "invalid value found on the device (G outside [0, capacity) or R > 3)"
+                                             : "device-side error");
+  }
+  return CORAL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t coral_net_floats(int32_t hidden) { return dense_floats(hidden); }
+
+int coral_params_default(coral_params* p) {
+  if (!p) return fail(nullptr, CORAL_E_INVALID, "params is NULL");
+  memset(p, 0, sizeof(*p));
+  p->hidden = 0;
+  p->path = CORAL_NET_FP32_PERCELL;
+  p->k_inv = 0.1f;
+  p->k_liq = 0.1f;
+  p->k_exp = 0.5f;
+  p->k_flow = 0.2f;
+  p->e_day = 0.005f;
+  p->e_night = 0.005f;
+  p->day_period = 200;
+  p->rotation = 1;
+  p->radiation_every = 0;
+  p->thr_mut = 0;
+  p->thr_merge = 0;
+  p->sigma_mut = 0.05f;
+  p->world = 0;
+  p->seed = 0;
+  p->fma_cutoff = 8;
+  p->max_mma_genomes = 2;
+  return CORAL_OK;
+}
+
+int coral_substrate_create(const coral_params* p, int32_t width, int32_t height, int32_t genome_capacity,
+                           void* cuda_stream, coral_substrate** out) {
+  if (!p || !out) return fail(nullptr, CORAL_E_INVALID, "NULL argument");
+  *out = nullptr;
+  if (width < 3 || height < 3) return fail(nullptr, CORAL_E_INVALID, "width and height must be >= 3");
+  if ((long long)width * height >= (1LL << 31)) return fail(nullptr, CORAL_E_INVALID, "width * height must be < 2^31");
+  if (genome_capacity < 1 || genome_capacity > (1 << 24))
+    return fail(nullptr, CORAL_E_INVALID, "genome_capacity must be in [1, 2^24]");
+  if (!valid_hidden(p->hidden)) return fail(nullptr, CORAL_E_INVALID, "hidden must be 0, 16, 32, 48 or 64");
+  if (p->path != CORAL_NET_FP32_PERCELL && p->path != CORAL_NET_BF16_GROUPED)
+    return fail(nullptr, CORAL_E_INVALID, "unknown path");
+  if (p->day_period < 1) return fail(nullptr, CORAL_E_INVALID, "day_period must be >= 1");
+  if (p->radiation_every < 0) return fail(nullptr, CORAL_E_INVALID, "radiation_every must be >= 0");
+  if (p->path == CORAL_NET_BF16_GROUPED && (p->max_mma_genomes < 1 || p->max_mma_genomes > 4))
+    return fail(nullptr, CORAL_E_INVALID, "max_mma_genomes must be in [1, 4]");
+  coral_substrate* s = nullptr;
+  try {
+    s = new coral_substrate();
+  } catch (...) {
+    return fail(nullptr, CORAL_E_OOM, "host allocation failed");
+  }
+  s->p = *p;
+  s->W = width;
+  s->H = height;
+  s->N = (long long)width * height;
+  s->cap = genome_capacity;
+  s->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int rc = CORAL_OK;
+  do {
+    cudaError_t e;
+    if ((e = cudaGetDevice(&s->device)) != cudaSuccess) { rc = cuda_fail(s, e, "cudaGetDevice"); break; }
+    if ((e = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, s->device)) != cudaSuccess) {
+      rc = cuda_fail(s, e, "cudaDeviceGetAttribute");
+      break;
+    }
+    const long long N = s->N;
+    bool ok = true;
+    for (int b = 0; b < 2 && ok; ++b) {
+      ok &= dalloc(s, &s->st[b].E, N) == cudaSuccess;
+      ok &= dalloc(s, &s->st[b].I, N) == cudaSuccess;
+      ok &= dalloc(s, &s->st[b].C, 4 * N) == cudaSuccess;
+      ok &= dalloc(s, &s->st[b].G, N) == cudaSuccess;
+      ok &= dalloc(s, &s->st[b].R, N) == cudaSuccess;
+    }
+    ok = ok && dalloc(s, &s->p1.keep, N) == cudaSuccess && dalloc(s, &s->p1.q, N) == cudaSuccess &&
+         dalloc(s, &s->p1.I1, N) == cudaSuccess && dalloc(s, &s->p1.xamt, N) == cudaSuccess &&
+         dalloc(s, &s->p1.xdir, N) == cudaSuccess;
+    s->g.hidden = p->hidden;
+    s->g.capacity = genome_capacity;
+    s->g.net_stride = net32_stride(p->hidden);
+    s->g.blob_bytes = bf16_blob_bytes(p->hidden);
+    ok = ok && dalloc(s, &s->g.genes, (size_t)genome_capacity * kGenes) == cudaSuccess &&
+         dalloc(s, &s->g.parent, (size_t)genome_capacity) == cudaSuccess &&
+         dalloc(s, &s->g.nets32, (size_t)genome_capacity * s->g.net_stride) == cudaSuccess &&
+         dalloc(s, &s->g.nets16, (size_t)genome_capacity * s->g.blob_bytes) == cudaSuccess;
+    ok = ok && dalloc(s, &s->part1, kMaxPartials) == cudaSuccess && dalloc(s, &s->part2, kMaxPartials) == cudaSuccess &&
+         dalloc(s, &s->ring, kRing) == cudaSuccess && dalloc(s, &s->status, 4) == cudaSuccess;
+    const int nblk = radiation_blocks(N);
+    ok = ok && dalloc(s, &s->count, genome_capacity) == cudaSuccess && dalloc(s, &s->blockcnt, nblk) == cudaSuccess &&
+         dalloc(s, &s->blockoff, nblk) == cudaSuccess && dalloc(s, &s->hits, genome_capacity) == cudaSuccess &&
+         dalloc(s, &s->hitbits, genome_capacity) == cudaSuccess &&
+         dalloc(s, &s->freelist, genome_capacity) == cudaSuccess &&
+         dalloc(s, &s->newslots, genome_capacity) == cudaSuccess && dalloc(s, &s->counters, 8) == cudaSuccess;
+    if (!ok) {
+      cudaGetLastError();
+      rc = fail(s, CORAL_E_OOM, "device allocation failed");
+      break;
+    }
+    if ((e = cudaMemset(s->status, 0, 4 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(s->ring, 0, kRing * sizeof(coral_stats))) != cudaSuccess ||
+        (e = cudaMemset(s->g.parent, 0xFF, sizeof(int32_t) * genome_capacity)) != cudaSuccess ||
+        (e = cudaMemset(s->g.genes, 0, sizeof(float) * kGenes * genome_capacity)) != cudaSuccess ||
+        (e = cudaMemset(s->g.nets32, 0, sizeof(float) * s->g.net_stride * (size_t)genome_capacity)) != cudaSuccess ||
+        (e = cudaMemset(s->g.nets16, 0, (size_t)s->g.blob_bytes * genome_capacity)) != cudaSuccess) {
+      rc = cuda_fail(s, e, "cudaMemset");
+      break;
+    }
+    s->grid1 = p->path == CORAL_NET_BF16_GROUPED ? pass1_bf16_grid(s->sms) : pass1_fp32_grid(s->sms);
+    s->grid2 = pass2_grid(s->sms);
+    if (s->grid1 < 1) {
+      rc = fail(s, CORAL_E_CUDA, "the BF16 tensor-core kernel cannot be launched on this device");
+      break;
+    }
+  } while (0);
+  if (rc != CORAL_OK) {
+    free_all(s);
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return CORAL_OK;
+}
+
+int coral_substrate_destroy(coral_substrate* s) {
+  if (!s) return CORAL_OK;
+  cudaStreamSynchronize(s->stream);
+  free_all(s);
+  delete s;
+  return CORAL_OK;
+}
+
+int coral_state_load(coral_substrate* s, const float* E, const float* I, const float* C, const int32_t* G,
+                     const uint8_t* R, int src_on_device) {
+  if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
+  const long long N = s->N;
+  const Planes& d = s->st[s->cur];
+  const cudaMemcpyKind k = kind_in(src_on_device);
+  if (E) CK(s, cudaMemcpyAsync(d.E, E, sizeof(float) * N, k, s->stream));
+  if (I) CK(s, cudaMemcpyAsync(d.I, I, sizeof(float) * N, k, s->stream));
+  if (C) CK(s, cudaMemcpyAsync(d.C, C, sizeof(float) * 4 * N, k, s->stream));
+  if (G) CK(s, cudaMemcpyAsync(d.G, G, sizeof(int32_t) * N, k, s->stream));
+  if (R) CK(s, cudaMemcpyAsync(d.R, R, N, k, s->stream));
+  if (G || R) CK(s, launch_validate_state(G ? d.G : nullptr, R ? d.R : nullptr, N, s->cap, s->status, s->stream));
+  // host sources may be pinned: the copies must finish before the caller regains the buffers
+  if (!src_on_device) CK(s, cudaStreamSynchronize(s->stream));
+  s->t = 0;
+  return CORAL_OK;
+}
+
+int coral_genome_table_load(coral_substrate* s, int32_t n, const float* genes, const float* dense,
+                            int src_on_device) {
+  if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
+  if (n < 1 || n > s->cap) return fail(s, CORAL_E_INVALID, "n must be in [1, genome_capacity]");
+  if (!genes && !dense) return fail(s, CORAL_E_INVALID, "need CPPN genes or dense nets");
+  const cudaMemcpyKind k = kind_in(src_on_device);
+  CK(s, cudaMemsetAsync(s->g.genes, 0, sizeof(float) * kGenes * (size_t)s->cap, s->stream));
+  CK(s, cudaMemsetAsync(s->g.parent, 0xFF, sizeof(int32_t) * (size_t)s->cap, s->stream));
+  CK(s, cudaMemsetAsync(s->g.nets32, 0, sizeof(float) * s->g.net_stride * (size_t)s->cap, s->stream));
+  CK(s, cudaMemsetAsync(s->g.nets16, 0, (size_t)s->g.blob_bytes * s->cap, s->stream));
+  if (genes) {
+    CK(s, cudaMemcpyAsync(s->g.genes, genes, sizeof(float) * kGenes * (size_t)n, k, s->stream));
+    if (!src_on_device) CK(s, cudaStreamSynchronize(s->stream));
+    s->has_cppn = true;
+  } else {
+    const size_t bytes = sizeof(float) * coral_net_floats(s->p.hidden) * (size_t)n;
+    float* tmp = nullptr;
+    CK(s, cudaMallocAsync((void**)&tmp, bytes, s->stream));
+    cudaError_t e = cudaMemcpyAsync(tmp, dense, bytes, k, s->stream);
+    if (e == cudaSuccess) e = launch_dense_pack(s->g, tmp, n, s->stream);
+    if (e == cudaSuccess) e = launch_bf16_pack(s->g, nullptr, nullptr, n, s->stream);
+    cudaFreeAsync(tmp, s->stream);
+    if (e == cudaSuccess && !src_on_device) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e, "dense net load");
+    s->has_cppn = false;
+  }
+  s->genomes_loaded = true;
+  return CORAL_OK;
+}
+
+int coral_cppn_generate_weights(coral_substrate* s, const int32_t* slots, int32_t n) {
+  if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
+  if (!s->has_cppn) return fail(s, CORAL_E_STATE, "no CPPN genes loaded");
+  if (n < 0 || n > s->cap) return fail(s, CORAL_E_INVALID, "n must be in [0, genome_capacity]");
+  if (n == 0) return CORAL_OK;
+  int32_t* dslots = nullptr;
+  if (slots) {
+    for (int i = 0; i < n; ++i)
+      if (slots[i] < 0 || slots[i] >= s->cap) return fail(s, CORAL_E_INVALID, "slot id out of range");
+    CK(s, cudaMemcpyAsync(s->newslots, slots, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s->stream));
+    dslots = s->newslots;
+  }
+  CK(s, launch_cppn_generate(s->g, dslots, nullptr, n, s->stream));
+  CK(s, launch_bf16_pack(s->g, dslots, nullptr, n, s->stream));
+  if (slots) CK(s, cudaStreamSynchronize(s->stream));   // the host slot list is consumed
+  return CORAL_OK;
+}
+
+int coral_step(coral_substrate* s, int32_t n_steps) {
+  if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
+  if (n_steps < 0) return fail(s, CORAL_E_INVALID, "n_steps must be >= 0");
+  if (!s->genomes_loaded) return fail(s, CORAL_E_STATE, "no genome table loaded");
+  if (s->p.radiation_every > 0 && !s->has_cppn)
+    return fail(s, CORAL_E_STATE, "radiation needs CPPN genomes (direct nets cannot mutate)");
+  for (int i = 0; i < n_steps; ++i) {
+    StepArgs a = step_args(s);
+    if (s->p.path == CORAL_NET_BF16_GROUPED)
+      CK(s, launch_pass1_bf16(a, s->stream, s->grid1));
+    else
+      CK(s, launch_pass1_fp32(a, s->stream, s->grid1));
+    CK(s, launch_pass2(a, s->stream, s->grid2));
+    CK(s, launch_stats(a, s->grid1, s->grid2, s->t, s->ring, s->stream));
+    s->cur ^= 1;
+    if (s->p.radiation_every > 0 && (s->t + 1) % s->p.radiation_every == 0) {
+      RadiationArgs r = {};
+      r.W = s->W;
+      r.H = s->H;
+      r.N = s->N;
+      r.G = s->st[s->cur].G;
+      r.g = s->g;
+      r.thr_mut = s->p.thr_mut;
+      r.thr_merge = s->p.thr_merge;
+      r.sigma = s->p.sigma_mut;
+      r.world = s->p.world;
+      r.seed = s->p.seed;
+      r.step = (uint32_t)s->t;
+      r.count = s->count;
+      r.blockcnt = s->blockcnt;
+      r.blockoff = s->blockoff;
+      r.hits = s->hits;
+      r.hitbits = s->hitbits;
+      r.max_hits = s->cap;
+      r.freelist = s->freelist;
+      r.newslots = s->newslots;
+      r.counters = s->counters;
+      r.rec = s->ring + (s->t % kRing);
+      CK(s, launch_radiation(r, s->stream));
+    }
+    ++s->t;
+  }
+  return CORAL_OK;
+}
+
+int coral_read_channels(coral_substrate* s, uint32_t mask, void* dst, size_t dst_bytes, int on_device) {
+  if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
+  if (!dst) return fail(s, CORAL_E_INVALID, "dst is NULL");
+  const long long N = s->N;
+  size_t need = 0;
+  for (int b = 0; b < 8; ++b)
+    if (mask & (1u << b)) need += (b == 7) ? (size_t)N : (size_t)N * 4;
+  if (dst_bytes < need) return fail(s, CORAL_E_CAPACITY, "dst_bytes too small for the selected planes");
+  const Planes& d = s->st[s->cur];
+  const cudaMemcpyKind k = kind_out(on_device);
+  char* o = static_cast<char*>(dst);
+  const void* src[8] = {d.E, d.I, d.C, d.C + N, d.C + 2 * N, d.C + 3 * N, d.G, d.R};
+  for (int b = 0; b < 8; ++b) {
+    if (!(mask & (1u << b))) continue;
+    const size_t bytes = (b == 7) ? (size_t)N : (size_t)N * 4;
+    CK(s, cudaMemcpyAsync(o, src[b], bytes, k, s->stream));
+    o += bytes;
+  }
+  return check_status(s);
+}
+
+int coral_read_stats(coral_substrate* s, int64_t step_from, int32_t n, coral_stats* out) {
+  if (!s || !out) return fail(s, CORAL_E_INVALID, "NULL argument");
+  if (n < 0 || step_from < 0 || step_from + n > s->t || step_from < s->t - kRing)
+    return fail(s, CORAL_E_INVALID, "requested steps are not in the stats ring");
+  int rc = check_status(s);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i)
+    CK(s, cudaMemcpy(out + i, s->ring + ((step_from + i) % kRing), sizeof(coral_stats), cudaMemcpyDeviceToHost));
+  return CORAL_OK;
+}
+
+int coral_read_perm(coral_substrate* s, int32_t* dst_counts, int32_t* dst_perm) {
+  if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
+  const long long N = s->N;
+  const int nblk = bucket_blocks(N);
+  if (!s->sort_buf) {
+    const size_t words = 5 * (size_t)N + 256 * (size_t)nblk + (size_t)s->cap + 64;
+    CK(s, dalloc(s, &s->sort_buf, words));
+  }
+  SortArgs a = {};
+  a.keys_in = s->st[s->cur].G;
+  a.N = N;
+  a.capacity = s->cap;
+  a.k0 = s->sort_buf;
+  a.v0 = a.k0 + N;
+  a.k1 = a.v0 + N;
+  a.v1 = a.k1 + N;
+  a.perm = a.v1 + N;
+  a.hist = a.perm + N;
+  a.count = a.hist + 256 * (size_t)nblk;
+  CK(s, launch_bucket(a, s->stream));
+  if (dst_counts) CK(s, cudaMemcpyAsync(dst_counts, a.count, sizeof(int32_t) * s->cap, cudaMemcpyDeviceToHost, s->stream));
+  if (dst_perm) CK(s, cudaMemcpyAsync(dst_perm, a.perm, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s->stream));
+  return check_status(s);
+}
+
+int coral_read_genomes(coral_substrate* s, float* genes, int32_t* parent) {
+  if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
+  if (genes) CK(s, cudaMemcpyAsync(genes, s->g.genes, sizeof(float) * kGenes * (size_t)s->cap, cudaMemcpyDeviceToHost, s->stream));
+  if (parent) CK(s, cudaMemcpyAsync(parent, s->g.parent, sizeof(int32_t) * (size_t)s->cap, cudaMemcpyDeviceToHost, s->stream));
+  return check_status(s);
+}
+
+int coral_read_weights(coral_substrate* s, int32_t slot, float* dst, size_t dst_floats) {
+  if (!s || !dst) return fail(s, CORAL_E_INVALID, "NULL argument");
+  if (slot < 0 || slot >= s->cap) return fail(s, CORAL_E_INVALID, "slot out of range");
+  const int nf = coral_net_floats(s->p.hidden);
+  if (dst_floats < (size_t)nf) return fail(s, CORAL_E_CAPACITY, "dst too small");
+  float* tmp = nullptr;
+  CK(s, cudaMallocAsync((void**)&tmp, sizeof(float) * nf, s->stream));
+  cudaError_t e = launch_read_dense(s->g, slot, tmp, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, tmp, sizeof(float) * nf, cudaMemcpyDeviceToHost, s->stream);
+  cudaFreeAsync(tmp, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "read weights");
+  return check_status(s);
+}
+
+int coral_set_step(coral_substrate* s, int64_t t) {
+  if (!s || t < 0) return fail(s, CORAL_E_INVALID, "bad argument");
+  s->t = t;
+  return CORAL_OK;
+}
+
+int coral_get_step(const coral_substrate* s, int64_t* t) {
+  if (!s || !t) return fail(nullptr, CORAL_E_INVALID, "NULL argument");
+  *t = s->t;
+  return CORAL_OK;
+}
+
+int coral_sync(coral_substrate* s) {
+  if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
+  return check_status(s);
+}
+
+const char* coral_last_error(const coral_substrate* s) { return s ? s->err.c_str() : g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,220 @@
+// Internal declarations of the GB300 substrate-step library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/coral.h"
+
+namespace coral {
+
+constexpr int kIn = 54;        // 9 kernel offsets x 6 sensor channels
+constexpr int kOut = 10;       // com0..3, invest, liquidate, explore0..3
+constexpr int kGenes = 18;     // CPPN genes
+constexpr int kRing = 4096;    // stats ring length (steps)
+constexpr int kMaxPartials = 8192;
+constexpr uint8_t kNoExplore = 4;
+
+// ---- FP32 net layout in device memory (one record per genome slot) ------------------------
+// hidden = 0: W[10][56] (columns 54,55 zero), b[12]
+// hidden = H: W1[H][56], b1[H rounded to 4], W2T[H][12] (hidden-major, 10 used), b2[12]
+__host__ __device__ inline int dense_floats(int H) {   // public dense layout length
+  return H ? H * kIn + H + kOut * H + kOut : kOut * kIn + kOut;
+}
+__host__ __device__ inline int net32_b1(int H) { return (H ? H : kOut) * 56; }
+__host__ __device__ inline int net32_w2t(int H) { return net32_b1(H) + ((H + 3) & ~3); }
+__host__ __device__ inline int net32_b2(int H) { return net32_w2t(H) + H * 12; }
+__host__ __device__ inline int net32_stride(int H) {
+  int n = H ? net32_b2(H) + 12 : net32_b1(0) + 12;
+  return (n + 15) & ~15;
+}
+
+// ---- BF16 tensor-core net blob (one per slot; byte image of the shared-memory operands) --
+// [0, n1*128)         W1 (or W for hidden = 0): n1 rows of 64 bf16 (K-major, 128-byte rows,
+//                     16-byte chunks XOR-swizzled by row & 7), K index = 6*rank + channel,
+//                     K = 54 holds the layer-1 bias (the A operand carries 1.0 there).
+// [n1*128, +2048)     W2: 16 rows x 64 bf16 (10 used), same swizzle; absent for hidden = 0.
+// then                b2 (or nothing for hidden = 0): 16 float32.
+__host__ __device__ inline int bf16_n1(int H) { return H ? H : 16; }
+__host__ __device__ inline int bf16_w2_off(int H) { return bf16_n1(H) * 128; }
+__host__ __device__ inline int bf16_b2_off(int H) { return H ? bf16_w2_off(H) + 16 * 128 : bf16_w2_off(H); }
+__host__ __device__ inline int bf16_blob_bytes(int H) {
+  int n = H ? bf16_b2_off(H) + 64 : bf16_w2_off(H);
+  return (n + 127) & ~127;
+}
+
+struct Planes {
+  float* E;
+  float* I;
+  float* C;        // 4 planes of N floats
+  int32_t* G;
+  uint8_t* R;
+};
+
+struct Pass1Bufs {
+  float* keep;     // E1 minus what the cell sends along infrastructure
+  float* q;        // k_flow * E1 / S (FP64 denominator), what each neighbour gets per unit I_t
+  float* I1;       // infrastructure after invest / liquidate
+  float* xamt;     // exploration amount (0 when not exploring)
+  uint8_t* xdir;   // exploration direction 0..3 (N,E,S,W) or kNoExplore
+};
+
+struct Partial {   // per-block partial sums of one step (FP64), fixed-order combined
+  double s[6];     // E, I, C0..C3
+  long long c[2];  // explore, takeover
+};
+
+struct StepArgs {
+  int W, H;
+  long long N;
+  int hidden;
+  int rotation;
+  float k_inv, k_liq, k_exp, k_flow;
+  int is_day;
+  float e_day, e_night;
+  Planes cur, nxt;
+  Pass1Bufs p1;
+  const float* nets32;
+  int net_stride;
+  const uint8_t* nets16;
+  int blob_bytes;
+  Partial* part1;   // written by pass 1 (C sums, explore count)
+  Partial* part2;   // written by pass 2 (E, I sums, takeover count)
+  int fma_cutoff;
+  int max_mma_genomes;
+  int* status;
+};
+
+// ---- Philox4x32-10 (Salmon et al., SC'11), written for the device -----------------------
+__host__ __device__ inline uint32_t mulhi32(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  return __umulhi(a, b);
+#else
+  return (uint32_t)(((uint64_t)a * b) >> 32);
+#endif
+}
+
+__host__ __device__ inline uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = mulhi32(0xD2511F53u, c.x);
+    const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = mulhi32(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Counter (cell, step, stream << 24 | sub, world), key = seed.
+__device__ inline uint4 draw(uint32_t cell, uint32_t step, uint32_t stream, uint32_t sub,
+                             uint32_t world, unsigned long long seed) {
+  return philox4x32_10(make_uint4(cell, step, (stream << 24) | (sub & 0xFFFFFFu), world),
+                       (uint32_t)seed, (uint32_t)(seed >> 32));
+}
+
+__device__ inline float uniform01f(uint32_t u) {  // ((u >> 8) + 0.5) * 2^-24, exact
+  return ((float)(u >> 8) + 0.5f) * 5.9604644775390625e-8f;
+}
+
+// ---- torus helpers -----------------------------------------------------------------------
+__device__ inline int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// Kernel rank p (1..8) -> octant offset from forward: 0, +1, -1, +2, -2, +3, -3, +4.
+__host__ __device__ constexpr int rank_delta(int p) {
+  return p == 1 ? 0 : p == 2 ? 1 : p == 3 ? -1 : p == 4 ? 2 : p == 5 ? -2 : p == 6 ? 3 : p == 7 ? -3 : 4;
+}
+
+// Octant o (0..7 clockwise from north: N, NE, E, SE, S, SW, W, NW) -> (dx, dy), north being
+// the row above; the offsets are packed two bits per octant as (d + 1).
+__host__ __device__ inline void octant_offset(int o, int& dx, int& dy) {
+  dx = (int)((0x1A9u >> (2 * o)) & 3u) - 1;
+  dy = (int)((0x1A90u >> (2 * o)) & 3u) - 1;
+}
+
+// Explore logit k -> quarter turns clockwise from the forward direction (fwd, right, left, back).
+__host__ __device__ constexpr int explore_turn(int k) { return k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 3 : 2; }
+
+// ---- reductions: FP32 within a warp (32 cells), FP64 above ------------------------------
+__device__ inline float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ inline int warp_sum_i(int v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---- launchers (defined in the .cu files) -----------------------------------------------
+cudaError_t launch_pass1_fp32(const StepArgs& a, cudaStream_t st, int grid);
+cudaError_t launch_pass1_bf16(const StepArgs& a, cudaStream_t st, int grid);
+cudaError_t launch_pass2(const StepArgs& a, cudaStream_t st, int grid);
+cudaError_t launch_stats(const StepArgs& a, int n_part1, int n_part2, long long t,
+                         coral_stats* ring, cudaStream_t st);
+int pass1_fp32_grid(int sms);
+int pass1_bf16_grid(int sms);
+int pass2_grid(int sms);
+size_t pass1_bf16_smem();
+
+struct GenomeArgs {
+  int hidden;
+  int capacity;
+  float* genes;       // [cap][18]
+  int32_t* parent;    // [cap]
+  float* nets32;      // [cap][net_stride]
+  int net_stride;
+  uint8_t* nets16;    // [cap][blob_bytes]
+  int blob_bytes;
+};
+cudaError_t launch_cppn_generate(const GenomeArgs& g, const int32_t* slots, const int* n_dev,
+                                 int n_host, cudaStream_t st);
+cudaError_t launch_dense_pack(const GenomeArgs& g, const float* dense, int n, cudaStream_t st);
+cudaError_t launch_bf16_pack(const GenomeArgs& g, const int32_t* slots, const int* n_dev,
+                             int n_host, cudaStream_t st);
+cudaError_t launch_read_dense(const GenomeArgs& g, int slot, float* dst, cudaStream_t st);
+cudaError_t launch_validate_state(const int32_t* G, const uint8_t* R, long long N, int cap,
+                                  int* status, cudaStream_t st);
+
+struct RadiationArgs {
+  int W, H;
+  long long N;
+  int32_t* G;                 // current state's G (rewritten in place for the children)
+  GenomeArgs g;
+  uint32_t thr_mut, thr_merge;
+  float sigma;
+  uint32_t world;
+  unsigned long long seed;
+  uint32_t step;
+  // scratch
+  int32_t* count;             // [cap]
+  int32_t* blockcnt;          // [nblk]
+  int32_t* blockoff;          // [nblk]
+  int4* hits;                 // [max_hits] (cell, parent, partner or -1, flags)
+  uint32_t* hitbits;          // [max_hits]
+  int max_hits;
+  int32_t* freelist;          // [cap]
+  int32_t* newslots;          // [cap]
+  int* counters;              // [8]: n_hits, n_free, n_assigned, n_mut, n_merge, n_live
+  coral_stats* rec;           // stats record of this step
+};
+cudaError_t launch_radiation(const RadiationArgs& r, cudaStream_t st);
+int radiation_blocks(long long N);
+
+struct SortArgs {
+  const int32_t* keys_in;     // [N]
+  long long N;
+  int capacity;
+  int32_t* count;             // [cap] output
+  int32_t* perm;              // [N] output
+  int32_t* k0; int32_t* v0;   // ping-pong scratch [N]
+  int32_t* k1; int32_t* v1;
+  int32_t* hist;              // [256 * nblk]
+};
+cudaError_t launch_bucket(const SortArgs& a, cudaStream_t st);
+int bucket_blocks(long long N);
+
+}  // namespace coral

@@ -1,0 +1,56 @@
+// Actuator epilogue shared by both network paths: from the ten activated actuator values of a
+// cell to its pass-1 outputs (Section "Experiment").
+#pragma once
+
+#include "coral_internal.cuh"
+
+namespace coral {
+
+struct CellOut {
+  float C[4];
+  float keep, q, I1, xamt;
+  uint8_t xdir;
+};
+
+// a[0..3] com, a[4] invest, a[5] liquidate, a[6..9] explore (fwd, right, left, back).
+// E, I: the cell's state; S: FP64 sum of I_t over its 4 von Neumann neighbours; r: rotation.
+__device__ __forceinline__ void actuator_epilogue(const StepArgs& p, const float* a, float E,
+                                                  float I, double S, int r, CellOut& o) {
+  // Communication: normalised by max(1, ||a0..3||) and passed through a sigmoid.
+  const float n2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3];
+  const float nrm = fmaxf(1.0f, sqrtf(n2));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) o.C[k] = 1.0f / (1.0f + expf(-(a[k] / nrm)));
+  // Invest moves inv*E into infrastructure, liquidate moves liq*I back into energy.
+  const float inv = p.k_inv * fmaxf(a[4], 0.0f);
+  const float liq = p.k_liq * fmaxf(a[5], 0.0f);
+  const float E1 = E - inv * E + liq * I;
+  const float I1 = I + inv * E - liq * I;
+  // Exploration toward the maximal explore actuator (first maximum on ties).
+  int k = 0;
+  float m = a[6];
+  if (a[7] > m) { k = 1; m = a[7]; }
+  if (a[8] > m) { k = 2; m = a[8]; }
+  if (a[9] > m) { k = 3; m = a[9]; }
+  const bool go = (m > 0.0f) && (I1 > 0.0f);
+  o.xdir = go ? (uint8_t)((r + explore_turn(k)) & 3) : kNoExplore;
+  o.xamt = go ? p.k_exp * m * I1 : 0.0f;
+  o.I1 = I1;
+  // Energy flow along infrastructure: the cell keeps (1 - k_flow) E1 when it has somewhere
+  // to send, and each neighbour j receives I_t(j) * q with q = k_flow E1 / S.
+  const bool send = S > 0.0;
+  o.keep = send ? E1 - p.k_flow * E1 : E1;
+  o.q = send ? (p.k_flow * E1) / (float)S : 0.0f;
+}
+
+__device__ __forceinline__ void store_pass1(const StepArgs& p, long long j, const CellOut& o) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) p.nxt.C[(long long)k * p.N + j] = o.C[k];
+  p.p1.keep[j] = o.keep;
+  p.p1.q[j] = o.q;
+  p.p1.I1[j] = o.I1;
+  p.p1.xamt[j] = o.xamt;
+  p.p1.xdir[j] = o.xdir;
+}
+
+}  // namespace coral

@@ -1,0 +1,520 @@
+// Genome table kernels: CPPN -> dense nets (HyperNEAT), FP32 / BF16 packing, radiation
+// (mutation and merge of CPPN genomes with slot allocation), and the stable counting sort of
+// cells by GenomeIndex.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "coral_internal.cuh"
+
+namespace coral {
+
+namespace {
+
+// ---------------------------------------------------------------------------------------
+// CPPN (Section "System Design": small CPPNs generate the weights and biases of the dense
+// net). Five inputs (x1, y1, x2, y2, 1), hidden sin / gauss / tanh, linear output.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ float cppn_eval(const float* g, float x1, float y1, float x2, float y2) {
+  float z[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    z[k] = g[5 * k] * x1 + g[5 * k + 1] * y1 + g[5 * k + 2] * x2 + g[5 * k + 3] * y2 + g[5 * k + 4];
+  return g[15] * sinf(z[0]) + g[16] * expf(-z[1] * z[1]) + g[17] * tanhf(z[2]);
+}
+
+__device__ __forceinline__ float layer_x(int i, int n) {
+  return n == 1 ? 0.0f : -1.0f + 2.0f * (float)i / (float)(n - 1);
+}
+
+// One block per listed slot; writes the slot's FP32 record (internal layout).
+__global__ void __launch_bounds__(256) k_cppn(GenomeArgs g, const int32_t* slots, const int* n_dev,
+                                             int n_host) {
+  const int n = n_dev ? *n_dev : n_host;
+  const int H = g.hidden;
+  __shared__ float gs[kGenes];
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int slot = slots ? slots[i] : i;
+    __syncthreads();
+    if (threadIdx.x < kGenes) gs[threadIdx.x] = g.genes[(long long)slot * kGenes + threadIdx.x];
+    __syncthreads();
+    float* rec = g.nets32 + (long long)slot * g.net_stride;
+    const float s1 = rsqrtf((float)kIn);
+    if (H == 0) {
+      for (int c = threadIdx.x; c < kOut * 56; c += blockDim.x) {
+        const int o = c / 56, i2 = c % 56;
+        rec[c] = i2 < kIn ? s1 * cppn_eval(gs, layer_x(i2, kIn), -1.0f, layer_x(o, kOut), 1.0f) : 0.0f;
+      }
+      for (int c = threadIdx.x; c < 12; c += blockDim.x)
+        rec[net32_b1(0) + c] = c < kOut ? s1 * cppn_eval(gs, 0.0f, 0.0f, layer_x(c, kOut), 1.0f) : 0.0f;
+      continue;
+    }
+    const float s2 = rsqrtf((float)H);
+    for (int c = threadIdx.x; c < H * 56; c += blockDim.x) {
+      const int h = c / 56, i2 = c % 56;
+      rec[c] = i2 < kIn ? s1 * cppn_eval(gs, layer_x(i2, kIn), -1.0f, layer_x(h, H), 0.0f) : 0.0f;
+    }
+    for (int c = threadIdx.x; c < ((H + 3) & ~3); c += blockDim.x)
+      rec[net32_b1(H) + c] = c < H ? s1 * cppn_eval(gs, 0.0f, 0.0f, layer_x(c, H), 0.0f) : 0.0f;
+    for (int c = threadIdx.x; c < H * 12; c += blockDim.x) {
+      const int h = c / 12, o = c % 12;
+      rec[net32_w2t(H) + c] = o < kOut ? s2 * cppn_eval(gs, layer_x(h, H), 0.0f, layer_x(o, kOut), 1.0f) : 0.0f;
+    }
+    for (int c = threadIdx.x; c < 12; c += blockDim.x)
+      rec[net32_b2(H) + c] = c < kOut ? s2 * cppn_eval(gs, 0.0f, 0.0f, layer_x(c, kOut), 1.0f) : 0.0f;
+  }
+}
+
+// Direct nets in the public dense layout -> internal FP32 records (slots 0..n-1).
+__global__ void __launch_bounds__(256) k_dense_pack(GenomeArgs g, const float* dense, int n) {
+  const int H = g.hidden;
+  const int nf = dense_floats(H);
+  for (int slot = blockIdx.x; slot < n; slot += gridDim.x) {
+    const float* src = dense + (long long)slot * nf;
+    float* rec = g.nets32 + (long long)slot * g.net_stride;
+    for (int c = threadIdx.x; c < g.net_stride; c += blockDim.x) rec[c] = 0.0f;
+    __syncthreads();
+    const int rows = H ? H : kOut;
+    for (int c = threadIdx.x; c < rows * kIn; c += blockDim.x) rec[(c / kIn) * 56 + c % kIn] = src[c];
+    const float* b1 = src + rows * kIn;
+    for (int c = threadIdx.x; c < rows; c += blockDim.x) rec[net32_b1(H) + c] = b1[c];
+    if (H) {
+      const float* w2 = b1 + H;   // [10][H]
+      for (int c = threadIdx.x; c < kOut * H; c += blockDim.x) {
+        const int o = c / H, h = c % H;
+        rec[net32_w2t(H) + h * 12 + o] = w2[c];
+      }
+      const float* b2 = w2 + kOut * H;
+      for (int c = threadIdx.x; c < kOut; c += blockDim.x) rec[net32_b2(H) + c] = b2[c];
+    }
+    __syncthreads();
+  }
+}
+
+// Internal FP32 record -> public dense layout (one slot).
+__global__ void k_read_dense(GenomeArgs g, int slot, float* dst) {
+  const int H = g.hidden;
+  const float* rec = g.nets32 + (long long)slot * g.net_stride;
+  const int rows = H ? H : kOut;
+  for (int c = threadIdx.x; c < rows * kIn; c += blockDim.x) dst[c] = rec[(c / kIn) * 56 + c % kIn];
+  float* b1 = dst + rows * kIn;
+  for (int c = threadIdx.x; c < rows; c += blockDim.x) b1[c] = rec[net32_b1(H) + c];
+  if (H) {
+    float* w2 = b1 + H;
+    for (int c = threadIdx.x; c < kOut * H; c += blockDim.x) w2[c] = rec[net32_w2t(H) + (c % H) * 12 + c / H];
+    float* b2 = w2 + kOut * H;
+    for (int c = threadIdx.x; c < kOut; c += blockDim.x) b2[c] = rec[net32_b2(H) + c];
+  }
+}
+
+// Byte offset of element (row, k) in a 128-byte-row K-major tile whose 16-byte chunks are
+// XOR-swizzled by (row & 7): the layout the tensor cores read with 128-byte swizzling.
+__device__ __forceinline__ int swz(int row, int k) {
+  return row * 128 + ((((k >> 3) ^ row) & 7) << 4) + ((k & 7) << 1);
+}
+
+// Internal FP32 record -> BF16 tensor-core blob (round to nearest even).
+__global__ void __launch_bounds__(256) k_bf16_pack(GenomeArgs g, const int32_t* slots, const int* n_dev,
+                                                  int n_host) {
+  const int n = n_dev ? *n_dev : n_host;
+  const int H = g.hidden;
+  const int n1 = bf16_n1(H);
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const int slot = slots ? slots[i] : i;
+    const float* rec = g.nets32 + (long long)slot * g.net_stride;
+    uint8_t* blob = g.nets16 + (long long)slot * g.blob_bytes;
+    const int rows1 = H ? H : kOut;
+    for (int c = threadIdx.x; c < n1 * 64; c += blockDim.x) {
+      const int row = c >> 6, k = c & 63;
+      float v = 0.0f;
+      if (row < rows1) v = k < kIn ? rec[row * 56 + k] : (k == kIn ? rec[net32_b1(H) + row] : 0.0f);
+      *reinterpret_cast<__nv_bfloat16*>(blob + swz(row, k)) = __float2bfloat16_rn(v);
+    }
+    if (H) {
+      uint8_t* w2 = blob + bf16_w2_off(H);
+      for (int c = threadIdx.x; c < 16 * 64; c += blockDim.x) {
+        const int o = c >> 6, k = c & 63;
+        const float v = (o < kOut && k < H) ? rec[net32_w2t(H) + k * 12 + o] : 0.0f;
+        *reinterpret_cast<__nv_bfloat16*>(w2 + swz(o, k)) = __float2bfloat16_rn(v);
+      }
+      float* b2 = reinterpret_cast<float*>(blob + bf16_b2_off(H));
+      for (int c = threadIdx.x; c < 16; c += blockDim.x) b2[c] = c < kOut ? rec[net32_b2(H) + c] : 0.0f;
+    }
+  }
+}
+
+__global__ void k_validate(const int32_t* G, const uint8_t* R, long long N, int cap, int* status) {
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N;
+       j += (long long)gridDim.x * blockDim.x) {
+    if ((G && (G[j] < 0 || G[j] >= cap)) || (R && R[j] > 3)) atomicCAS(status, 0, (int)CORAL_E_INVALID);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Radiation (Fig. 1 C: radiation of the substrate mutates CPPN genomes; Section "System
+// Design": mutation and crossover operators of NEAT applied via the physics).
+// ---------------------------------------------------------------------------------------
+constexpr int kRadThreads = 256;
+constexpr int kRadPerThread = 8;
+constexpr int kRadTile = kRadThreads * kRadPerThread;
+
+struct Hit {
+  bool hit, mut, merge;
+  int32_t g, gp;
+  uint32_t bits;
+};
+
+__device__ __forceinline__ Hit radiation_hit(const RadiationArgs& r, long long j) {
+  Hit h = {false, false, false, 0, -1, 0};
+  const uint32_t cell = (uint32_t)j;
+  if (r.thr_mut) h.mut = draw(cell, r.step, 0, 0, r.world, r.seed).x < r.thr_mut;
+  if (r.thr_merge) {
+    const uint4 w = draw(cell, r.step, 1, 0, r.world, r.seed);
+    if (w.x < r.thr_merge) {
+      const int x = (int)(j % r.W), y = (int)(j / r.W);
+      int dx, dy;
+      octant_offset(2 * (int)(w.y & 3u), dx, dy);     // von Neumann N, E, S, W
+      const long long n = (long long)wrap(y + dy, r.H) * r.W + wrap(x + dx, r.W);
+      const int32_t gp = r.G[n];
+      if (gp != r.G[j]) {
+        h.merge = true;
+        h.gp = gp;
+        h.bits = w.z;
+      }
+    }
+  }
+  h.hit = h.mut || h.merge;
+  if (h.hit) h.g = r.G[j];
+  return h;
+}
+
+// Exclusive block scan of one int per thread (blockDim = kRadThreads).
+__device__ __forceinline__ int block_exscan(int v, int& total) {
+  __shared__ int warp_tot[kRadThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_tot[w] = inc;
+  __syncthreads();
+  int before = 0;
+  total = 0;
+  for (int i = 0; i < kRadThreads / 32; ++i) {
+    if (i < w) before += warp_tot[i];
+    total += warp_tot[i];
+  }
+  __syncthreads();
+  return before + inc - v;
+}
+
+__global__ void __launch_bounds__(kRadThreads) k_rad_count(RadiationArgs r) {
+  const long long base = (long long)blockIdx.x * kRadTile + (long long)threadIdx.x * kRadPerThread;
+  int nh = 0, nm = 0, ng = 0;
+  for (int i = 0; i < kRadPerThread; ++i) {
+    const long long j = base + i;
+    if (j >= r.N) break;
+    const Hit h = radiation_hit(r, j);
+    nh += h.hit;
+    nm += h.mut;
+    ng += h.merge;
+  }
+  int tot;
+  block_exscan(nh, tot);
+  int tm, tg;
+  block_exscan(nm, tm);
+  block_exscan(ng, tg);
+  if (threadIdx.x == 0) {
+    r.blockcnt[blockIdx.x] = tot;
+    if (tm) atomicAdd(&r.counters[3], tm);
+    if (tg) atomicAdd(&r.counters[4], tg);
+  }
+}
+
+// Exclusive scan of n ints by one block (fixed order); total into *total.
+__global__ void __launch_bounds__(1024) k_scan(const int32_t* in, int32_t* out, long long n, int* total) {
+  __shared__ int part[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (long long b0 = 0; b0 < n; b0 += 1024LL * 16) {
+    // each thread owns 16 consecutive entries of this chunk
+    const long long s = b0 + (long long)threadIdx.x * 16;
+    int loc = 0;
+    for (int i = 0; i < 16; ++i)
+      if (s + i < n) loc += in[s + i];
+    part[threadIdx.x] = loc;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const int t = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+      __syncthreads();
+      part[threadIdx.x] += t;
+      __syncthreads();
+    }
+    int run = carry + part[threadIdx.x] - loc;
+    for (int i = 0; i < 16; ++i)
+      if (s + i < n) {
+        const int v = in[s + i];
+        out[s + i] = run;
+        run += v;
+      }
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += part[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+__global__ void __launch_bounds__(kRadThreads) k_rad_emit(RadiationArgs r) {
+  const long long base = (long long)blockIdx.x * kRadTile + (long long)threadIdx.x * kRadPerThread;
+  Hit hs[kRadPerThread];
+  int nh = 0;
+  for (int i = 0; i < kRadPerThread; ++i) {
+    const long long j = base + i;
+    hs[i] = j < r.N ? radiation_hit(r, j) : Hit{false, false, false, 0, -1, 0};
+    nh += hs[i].hit;
+  }
+  int tot;
+  int pos = r.blockoff[blockIdx.x] + block_exscan(nh, tot);
+  for (int i = 0; i < kRadPerThread; ++i) {
+    if (!hs[i].hit) continue;
+    if (pos < r.max_hits) {
+      r.hits[pos] = make_int4((int)(base + i), hs[i].g, hs[i].merge ? hs[i].gp : -1,
+                              (hs[i].mut ? 1 : 0) | (hs[i].merge ? 2 : 0));
+      r.hitbits[pos] = hs[i].bits;
+    }
+    ++pos;
+  }
+}
+
+__global__ void k_hist(const int32_t* G, long long N, int32_t* count) {
+  const int lane = threadIdx.x & 31;
+  const long long wbase = ((long long)blockIdx.x * blockDim.x + threadIdx.x) - lane;
+  const long long wstride = (long long)gridDim.x * blockDim.x;
+  for (long long b = wbase; b < N; b += wstride) {
+    const long long j = b + lane;
+    const int g = j < N ? G[j] : -1;
+    const unsigned m = __match_any_sync(0xffffffffu, g);
+    if (g >= 0 && lane == __ffs(m) - 1) atomicAdd(&count[g], __popc(m));
+  }
+}
+
+// Free slots (count 0) in increasing order; live count.
+__global__ void __launch_bounds__(1024) k_free(RadiationArgs r) {
+  __shared__ int wt[32];
+  __shared__ int carry, live;
+  if (threadIdx.x == 0) carry = live = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int s0 = 0; s0 < r.g.capacity; s0 += 1024) {
+    const int s = s0 + threadIdx.x;
+    const bool fr = s < r.g.capacity && r.count[s] == 0;
+    const bool lv = s < r.g.capacity && r.count[s] > 0;
+    const unsigned b = __ballot_sync(0xffffffffu, fr);
+    const int lv_w = __popc(__ballot_sync(0xffffffffu, lv));
+    if (lane == 0) wt[w] = __popc(b);
+    if (lane == 0 && lv_w) atomicAdd(&live, lv_w);
+    __syncthreads();
+    int before = 0, tot = 0;
+    for (int i = 0; i < 32; ++i) {
+      if (i < w) before += wt[i];
+      tot += wt[i];
+    }
+    if (fr) r.freelist[carry + before + __popc(b & ((1u << lane) - 1))] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    r.counters[1] = carry;
+    r.counters[5] = live;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_rad_assign(RadiationArgs r) {
+  const int nh = r.counters[0];
+  const int nf = r.counters[1];
+  int na = nh < nf ? nh : nf;
+  if (na > r.max_hits) na = r.max_hits;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < na; i += gridDim.x * blockDim.x) {
+    const int4 h = r.hits[i];
+    const int slot = r.freelist[i];
+    float c[kGenes];
+    const float* gp = r.g.genes + (long long)h.y * kGenes;
+#pragma unroll
+    for (int k = 0; k < kGenes; ++k) c[k] = gp[k];
+    if (h.w & 2) {
+      const uint32_t bits = r.hitbits[i];
+      const float* gq = r.g.genes + (long long)h.z * kGenes;
+#pragma unroll
+      for (int k = 0; k < kGenes; ++k)
+        if ((bits >> k) & 1u) c[k] = gq[k];
+    }
+    if (h.w & 1) {
+      uint32_t u[20];
+#pragma unroll
+      for (int sub = 0; sub < 5; ++sub) {
+        const uint4 w = draw((uint32_t)h.x, r.step, 2, sub, r.world, r.seed);
+        u[4 * sub] = w.x; u[4 * sub + 1] = w.y; u[4 * sub + 2] = w.z; u[4 * sub + 3] = w.w;
+      }
+#pragma unroll
+      for (int k = 0; k < kGenes / 2; ++k) {
+        // Box-Muller (Box & Muller, 1958) on two open-interval uniforms
+        const float rr = sqrtf(-2.0f * logf(uniform01f(u[2 * k])));
+        float sn, cs;
+        sincospif(2.0f * uniform01f(u[2 * k + 1]), &sn, &cs);
+        c[2 * k] += r.sigma * (rr * cs);
+        c[2 * k + 1] += r.sigma * (rr * sn);
+      }
+    }
+    float* dst = r.g.genes + (long long)slot * kGenes;
+#pragma unroll
+    for (int k = 0; k < kGenes; ++k) dst[k] = c[k];
+    r.g.parent[slot] = h.y;
+    r.G[h.x] = slot;
+    r.newslots[i] = slot;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    r.counters[2] = na;
+    coral_stats* s = r.rec;
+    s->n_mut = r.counters[3];
+    s->n_merge = r.counters[4];
+    s->n_born = na;
+    s->n_skipped = nh - na;
+    s->n_live = r.counters[5] + na;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Bucketing: stable counting sort of cell ids by GenomeIndex, as least-significant-digit
+// passes of stable 256-bucket counting sorts.
+// ---------------------------------------------------------------------------------------
+constexpr int kSortThreads = 256;
+constexpr int kSortTile = 4096;
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const int32_t* keys, long long N, int shift,
+                                                          int32_t* hist, int nblk) {
+  __shared__ int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * kSortTile;
+  for (int i = threadIdx.x; i < kSortTile; i += kSortThreads) {
+    const long long j = base + i;
+    if (j < N) atomicAdd(&h[(keys[j] >> shift) & 255], 1);
+  }
+  __syncthreads();
+  hist[(long long)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const int32_t* kin, const int32_t* vin,
+                                                             int32_t* kout, int32_t* vout, long long N,
+                                                             int shift, const int32_t* off, int nblk) {
+  __shared__ int wcnt[kSortThreads / 32][257];
+  __shared__ int run[256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  run[threadIdx.x] = off[(long long)threadIdx.x * nblk + blockIdx.x];
+  for (int i = 0; i < kSortThreads / 32; ++i) wcnt[i][threadIdx.x] = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * kSortTile;
+  for (int c0 = 0; c0 < kSortTile; c0 += kSortThreads) {
+    const long long j = base + c0 + threadIdx.x;
+    const bool ok = j < N;
+    const int key = ok ? kin[j] : 0;
+    const int val = ok ? (vin ? vin[j] : (int)j) : 0;
+    const int d = ok ? (key >> shift) & 255 : 256;
+    const unsigned m = __match_any_sync(0xffffffffu, d);
+    const int rank = __popc(m & ((1u << lane) - 1));
+    if (lane == __ffs(m) - 1) wcnt[w][d] = __popc(m);
+    __syncthreads();
+    if (ok) {
+      int pre = 0;
+      for (int i = 0; i < w; ++i) pre += wcnt[i][d];
+      const int pos = run[d] + pre + rank;
+      kout[pos] = key;
+      vout[pos] = val;
+    }
+    __syncthreads();
+    int add = 0;
+    for (int i = 0; i < kSortThreads / 32; ++i) {
+      add += wcnt[i][threadIdx.x];
+      wcnt[i][threadIdx.x] = 0;
+    }
+    run[threadIdx.x] += add;
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+int radiation_blocks(long long N) { return (int)((N + kRadTile - 1) / kRadTile); }
+int bucket_blocks(long long N) { return (int)((N + kSortTile - 1) / kSortTile); }
+
+cudaError_t launch_cppn_generate(const GenomeArgs& g, const int32_t* slots, const int* n_dev, int n_host,
+                                 cudaStream_t st) {
+  const int grid = n_dev ? 512 : (n_host < 1 ? 1 : (n_host > 4096 ? 4096 : n_host));
+  k_cppn<<<grid, 256, 0, st>>>(g, slots, n_dev, n_host);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dense_pack(const GenomeArgs& g, const float* dense, int n, cudaStream_t st) {
+  k_dense_pack<<<n < 4096 ? n : 4096, 256, 0, st>>>(g, dense, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bf16_pack(const GenomeArgs& g, const int32_t* slots, const int* n_dev, int n_host,
+                             cudaStream_t st) {
+  const int grid = n_dev ? 512 : (n_host < 1 ? 1 : (n_host > 4096 ? 4096 : n_host));
+  k_bf16_pack<<<grid, 256, 0, st>>>(g, slots, n_dev, n_host);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_read_dense(const GenomeArgs& g, int slot, float* dst, cudaStream_t st) {
+  k_read_dense<<<1, 256, 0, st>>>(g, slot, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_state(const int32_t* G, const uint8_t* R, long long N, int cap, int* status,
+                                  cudaStream_t st) {
+  k_validate<<<1024, 256, 0, st>>>(G, R, N, cap, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_radiation(const RadiationArgs& r, cudaStream_t st) {
+  const int nblk = radiation_blocks(r.N);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(r.count, 0, sizeof(int32_t) * r.g.capacity, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(r.counters, 0, sizeof(int) * 8, st)) != cudaSuccess) return e;
+  k_hist<<<1024, 256, 0, st>>>(r.G, r.N, r.count);
+  k_rad_count<<<nblk, kRadThreads, 0, st>>>(r);
+  k_scan<<<1, 1024, 0, st>>>(r.blockcnt, r.blockoff, nblk, &r.counters[0]);
+  k_rad_emit<<<nblk, kRadThreads, 0, st>>>(r);
+  k_free<<<1, 1024, 0, st>>>(r);
+  k_rad_assign<<<64, 128, 0, st>>>(r);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_cppn_generate(r.g, r.newslots, &r.counters[2], 0, st)) != cudaSuccess) return e;
+  return launch_bf16_pack(r.g, r.newslots, &r.counters[2], 0, st);
+}
+
+cudaError_t launch_bucket(const SortArgs& a, cudaStream_t st) {
+  const int nblk = bucket_blocks(a.N);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(a.count, 0, sizeof(int32_t) * a.capacity, st)) != cudaSuccess) return e;
+  k_hist<<<1024, 256, 0, st>>>(a.keys_in, a.N, a.count);
+  int passes = 1;
+  while (passes < 4 && (1LL << (8 * passes)) < (long long)a.capacity) ++passes;
+  const int32_t* kin = a.keys_in;
+  const int32_t* vin = nullptr;
+  for (int p = 0; p < passes; ++p) {
+    int32_t* kout = (p & 1) ? a.k1 : a.k0;
+    int32_t* vout = (p + 1 == passes) ? a.perm : ((p & 1) ? a.v1 : a.v0);
+    k_sort_hist<<<nblk, kSortThreads, 0, st>>>(kin, a.N, 8 * p, a.hist, nblk);
+    k_scan<<<1, 1024, 0, st>>>(a.hist, a.hist, 256LL * nblk, nullptr);
+    k_sort_scatter<<<nblk, kSortThreads, 0, st>>>(kin, vin, kout, vout, a.N, 8 * p, a.hist, nblk);
+    kin = kout;
+    vin = vout;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace coral

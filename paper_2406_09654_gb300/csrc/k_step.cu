@@ -1,0 +1,271 @@
+// Plain FP32 per-cell network (pass 1), physics stencil (pass 2) and the per-step FP64 totals.
+#include <math.h>
+
+#include "coral_internal.cuh"
+#include "epilogue.cuh"
+
+namespace coral {
+
+namespace {
+
+constexpr int kP1Threads = 128;
+constexpr int kP2Threads = 256;
+
+__device__ __forceinline__ void load6(const Planes& s, long long n, long long N, float* dst) {
+  dst[0] = __ldg(s.E + n);
+  dst[1] = __ldg(s.I + n);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) dst[2 + c] = __ldg(s.C + (long long)c * N + n);
+}
+
+// Sums one value per thread into a per-warp FP64 accumulator held by lane 0.
+__device__ __forceinline__ void warp_accumulate(float v, double& acc) {
+  v = warp_sum(v);
+  if ((threadIdx.x & 31) == 0) acc += (double)v;
+}
+
+// Combines the lane-0 accumulators of all warps of the block in warp order.
+template <int NS, int NC>
+__device__ void block_partial(const double (&s)[NS], const long long (&c)[NC], Partial* out,
+                              int s_first, int c_first) {
+  __shared__ double ss[32][6];
+  __shared__ long long sc[32][2];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    for (int k = 0; k < NS; ++k) ss[w][k] = s[k];
+    for (int k = 0; k < NC; ++k) sc[w][k] = c[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    Partial p = {};
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+      for (int k = 0; k < NS; ++k) p.s[s_first + k] += ss[i][k];
+      for (int k = 0; k < NC; ++k) p.c[c_first + k] += sc[i][k];
+    }
+    out[blockIdx.x] = p;
+  }
+}
+
+// One thread per cell: gather the rotation-ordered 3x3 neighbourhood of the six sensor
+// channels straight from the SoA planes, run the FP32 net with FMA, apply the actuators.
+__global__ void __launch_bounds__(kP1Threads) k_pass1_fp32(const StepArgs a) {
+  const int W = a.W, H = a.H;
+  const long long N = a.N;
+  double accC[4] = {0, 0, 0, 0};
+  long long accX[1] = {0};
+  const long long stride = (long long)gridDim.x * kP1Threads;
+  for (long long base = (long long)blockIdx.x * kP1Threads; base < N; base += stride) {
+    const long long j = base + threadIdx.x;
+    const bool valid = j < N;
+    CellOut o;
+    o.C[0] = o.C[1] = o.C[2] = o.C[3] = 0.0f;
+    o.xdir = kNoExplore;
+    if (valid) {
+      const int x = (int)(j % W), y = (int)(j / W);
+      const int r = a.rotation ? (int)a.cur.R[j] : 0;
+      float in[kIn];
+      load6(a.cur, j, N, in);
+#pragma unroll
+      for (int p = 1; p < 9; ++p) {
+        int dx, dy;
+        octant_offset((2 * r + rank_delta(p)) & 7, dx, dy);
+        const long long n = (long long)wrap(y + dy, H) * W + wrap(x + dx, W);
+        load6(a.cur, n, N, in + 6 * p);
+      }
+      const float* net = a.nets32 + (long long)a.cur.G[j] * a.net_stride;
+      float act[kOut];
+      if (a.hidden == 0) {
+#pragma unroll
+        for (int oo = 0; oo < kOut; ++oo) {
+          const float4* w = reinterpret_cast<const float4*>(net + oo * 56);
+          float acc = __ldg(net + net32_b1(0) + oo);
+#pragma unroll
+          for (int q = 0; q < 13; ++q) {
+            const float4 w4 = __ldg(w + q);
+            acc = fmaf(w4.x, in[4 * q], acc);
+            acc = fmaf(w4.y, in[4 * q + 1], acc);
+            acc = fmaf(w4.z, in[4 * q + 2], acc);
+            acc = fmaf(w4.w, in[4 * q + 3], acc);
+          }
+          const float4 w4 = __ldg(w + 13);
+          acc = fmaf(w4.x, in[52], acc);
+          acc = fmaf(w4.y, in[53], acc);
+          act[oo] = tanhf(acc);
+        }
+      } else {
+        const int Hd = a.hidden;
+        const float* b1 = net + net32_b1(Hd);
+        const float* w2t = net + net32_w2t(Hd);
+        const float* b2 = net + net32_b2(Hd);
+        float acc2[kOut];
+#pragma unroll
+        for (int oo = 0; oo < kOut; ++oo) acc2[oo] = __ldg(b2 + oo);
+        for (int k = 0; k < Hd; ++k) {
+          const float4* w = reinterpret_cast<const float4*>(net + k * 56);
+          float acc = __ldg(b1 + k);
+#pragma unroll
+          for (int q = 0; q < 13; ++q) {
+            const float4 w4 = __ldg(w + q);
+            acc = fmaf(w4.x, in[4 * q], acc);
+            acc = fmaf(w4.y, in[4 * q + 1], acc);
+            acc = fmaf(w4.z, in[4 * q + 2], acc);
+            acc = fmaf(w4.w, in[4 * q + 3], acc);
+          }
+          const float4 w4 = __ldg(w + 13);
+          acc = fmaf(w4.x, in[52], acc);
+          acc = fmaf(w4.y, in[53], acc);
+          const float h = tanhf(acc);
+          const float4* u = reinterpret_cast<const float4*>(w2t + k * 12);
+          const float4 u0 = __ldg(u), u1 = __ldg(u + 1), u2 = __ldg(u + 2);
+          acc2[0] = fmaf(u0.x, h, acc2[0]);
+          acc2[1] = fmaf(u0.y, h, acc2[1]);
+          acc2[2] = fmaf(u0.z, h, acc2[2]);
+          acc2[3] = fmaf(u0.w, h, acc2[3]);
+          acc2[4] = fmaf(u1.x, h, acc2[4]);
+          acc2[5] = fmaf(u1.y, h, acc2[5]);
+          acc2[6] = fmaf(u1.z, h, acc2[6]);
+          acc2[7] = fmaf(u1.w, h, acc2[7]);
+          acc2[8] = fmaf(u2.x, h, acc2[8]);
+          acc2[9] = fmaf(u2.y, h, acc2[9]);
+        }
+#pragma unroll
+        for (int oo = 0; oo < kOut; ++oo) act[oo] = tanhf(acc2[oo]);
+      }
+      // FP64 flow denominator: I_t of the von Neumann neighbours (kernel ranks 1, 4, 5, 8).
+      const double S = (double)in[7] + (double)in[25] + (double)in[31] + (double)in[49];
+      actuator_epilogue(a, act, in[0], in[1], S, r, o);
+      store_pass1(a, j, o);
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) warp_accumulate(valid ? o.C[k] : 0.0f, accC[k]);
+    const int ex = warp_sum_i(valid && o.xdir != kNoExplore ? 1 : 0);
+    if ((threadIdx.x & 31) == 0) accX[0] += ex;
+  }
+  block_partial<4, 1>(accC, accX, a.part1, 2, 0);
+}
+
+// Pass 2: exploration resolve and takeover, energy flow, day/night (one thread per cell).
+__global__ void __launch_bounds__(kP2Threads) k_pass2(const StepArgs a) {
+  const int W = a.W, H = a.H;
+  const long long N = a.N;
+  double acc[2] = {0, 0};
+  long long accT[1] = {0};
+  const long long stride = (long long)gridDim.x * kP2Threads;
+  for (long long base = (long long)blockIdx.x * kP2Threads; base < N; base += stride) {
+    const long long j = base + threadIdx.x;
+    const bool valid = j < N;
+    float E3 = 0.0f, I2 = 0.0f;
+    bool take = false;
+    if (valid) {
+      const int x = (int)(j % W), y = (int)(j / W);
+      const long long yW = (long long)y * W;
+      const long long nb[4] = {(long long)wrap(y - 1, H) * W + x, yW + wrap(x + 1, W),
+                               (long long)wrap(y + 1, H) * W + x, yW + wrap(x - 1, W)};
+      const float I1 = a.p1.I1[j];
+      I2 = I1 - a.p1.xamt[j];
+      float best = -INFINITY;
+      int bd = -1;
+#pragma unroll
+      for (int D = 0; D < 4; ++D) {
+        if (a.p1.xdir[nb[D]] == (uint8_t)((D + 2) & 3)) {   // neighbour explores toward j
+          const float xi = a.p1.xamt[nb[D]];
+          I2 += xi;
+          if (xi > best) { best = xi; bd = D; }             // strict: N, E, S, W keep ties
+        }
+      }
+      take = bd >= 0 && best > I1;
+      int32_t g = a.cur.G[j];
+      uint8_t r = a.cur.R[j];
+      if (take) {
+        g = a.cur.G[nb[bd]];
+        r = a.p1.xdir[nb[bd]];
+      }
+      const float inflow = ((a.p1.q[nb[0]] + a.p1.q[nb[1]]) + a.p1.q[nb[2]]) + a.p1.q[nb[3]];
+      const float E2 = a.p1.keep[j] + a.cur.I[j] * inflow;
+      E3 = a.is_day ? E2 + a.e_day : E2 - a.e_night * E2;
+      a.nxt.E[j] = E3;
+      a.nxt.I[j] = I2;
+      a.nxt.G[j] = g;
+      a.nxt.R[j] = r;
+    }
+    warp_accumulate(E3, acc[0]);
+    warp_accumulate(I2, acc[1]);
+    const int tk = warp_sum_i(take ? 1 : 0);
+    if ((threadIdx.x & 31) == 0) accT[0] += tk;
+  }
+  block_partial<2, 1>(acc, accT, a.part2, 0, 1);
+}
+
+// Fixed-order FP64 combination of the block partials into the stats ring.
+__global__ void __launch_bounds__(256) k_stats(const Partial* p1, int n1, const Partial* p2, int n2,
+                                              long long t, coral_stats* ring) {
+  __shared__ double ss[256][6];
+  __shared__ long long sc[256][2];
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  long long c[2] = {0, 0};
+  for (int i = threadIdx.x; i < n1; i += 256) {
+    for (int k = 2; k < 6; ++k) s[k] += p1[i].s[k];
+    c[0] += p1[i].c[0];
+  }
+  for (int i = threadIdx.x; i < n2; i += 256) {
+    s[0] += p2[i].s[0];
+    s[1] += p2[i].s[1];
+    c[1] += p2[i].c[1];
+  }
+  for (int k = 0; k < 6; ++k) ss[threadIdx.x][k] = s[k];
+  sc[threadIdx.x][0] = c[0];
+  sc[threadIdx.x][1] = c[1];
+  __syncthreads();
+  for (int h = 128; h; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      for (int k = 0; k < 6; ++k) ss[threadIdx.x][k] += ss[threadIdx.x + h][k];
+      sc[threadIdx.x][0] += sc[threadIdx.x + h][0];
+      sc[threadIdx.x][1] += sc[threadIdx.x + h][1];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    coral_stats r;
+    r.step = t;
+    r.sum_E = ss[0][0];
+    r.sum_I = ss[0][1];
+    for (int k = 0; k < 4; ++k) r.sum_C[k] = ss[0][2 + k];
+    r.n_explore = sc[0][0];
+    r.n_takeover = sc[0][1];
+    r.n_live = -1;
+    r.n_mut = r.n_merge = r.n_born = r.n_skipped = 0;
+    ring[t % kRing] = r;
+  }
+}
+
+int occupancy_grid(const void* fn, int threads, size_t smem, int sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  int g = per_sm * sms;
+  return g > kMaxPartials ? kMaxPartials : g;
+}
+
+}  // namespace
+
+int pass1_fp32_grid(int sms) { return occupancy_grid((const void*)k_pass1_fp32, kP1Threads, 0, sms); }
+int pass2_grid(int sms) { return occupancy_grid((const void*)k_pass2, kP2Threads, 0, sms); }
+
+cudaError_t launch_pass1_fp32(const StepArgs& a, cudaStream_t st, int grid) {
+  k_pass1_fp32<<<grid, kP1Threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass2(const StepArgs& a, cudaStream_t st, int grid) {
+  k_pass2<<<grid, kP2Threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const StepArgs& a, int n1, int n2, long long t, coral_stats* ring,
+                         cudaStream_t st) {
+  k_stats<<<1, 256, 0, st>>>(a.part1, n1, a.part2, n2, t, ring);
+  return cudaGetLastError();
+}
+
+}  // namespace coral
