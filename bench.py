@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Throughput of the Coralai substrate step on GB300: cell-updates/s.
+
+Default workload: the 4096x4096 torus with 1024 Zipf(1.2) genomes on Hilbert-curve blobs,
+54->64->10 CPPN nets, merge + mutation every 20 steps (radiation runs inside the timed steps).
+The state (16.8 M cells x 29 B = 487 MB, double-buffered) is larger than the 129 MB L2, so no
+flush is needed between steps. One JSON line on stdout (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--path bf16|fp32|auto]
+                  [--workload cfg3|cfg2|cfg1] [--impl coral|reference]
+
+N > 1 (under torchrun): every rank steps its own independent world (seed = rank), no
+data-path collective; the time is the max over ranks and the value counts all ranks' cells.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-updates/sec per GB300 (BF16 grouped vs FP32 plain) at stated tol; p50/p99 step latency"
+WORKLOADS = {
+    "cfg3": "4096x4096 torus, 1024 Zipf(1.2) genomes on Hilbert blobs, 54->64->10 CPPN nets, "
+            "merge+mutation every 20 steps",
+    "cfg2": "1024x1024 torus, 64 Voronoi genomes, 54->32->10 CPPN nets, mutation every 50 steps",
+    "cfg1": "64x64 torus, 8 Voronoi genomes, direct 54->10 nets",
+}
+STATE_BYTES = 29          # E, I, C0..C3 float32 + G int32 + R uint8 per cell
+P1_BYTES = 45             # pass 1 reads the state (29 B) and writes C' (16 B)
+P2_BYTES = 13             # pass 2 writes E', I' (float32), G' (int32), R' (uint8)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=60)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="coral", choices=["coral", "reference"])
+    ap.add_argument("--path", default="auto", choices=["auto", "bf16", "fp32"])
+    ap.add_argument("--workload", default="cfg3", choices=list(WORKLOADS))
+    ap.add_argument("--fp32-steps", type=int, default=12, help="steps of the FP32 comparison run")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- distributed
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if _cuda() else "gloo"
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def _cuda():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """Max of a float over all ranks (the job's time is its slowest rank's)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        res = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return res
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [v.strip() for v in line.split(",")]
+                if len(f) >= 7:
+                    rows.append(f)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        if not rows:
+            return res
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        res.update(sm_mhz=statistics.median(sm) if sm else None,
+                   sm_max_mhz=float(rows[0][1]) if rows[0][1].replace(".", "").isdigit() else None,
+                   reasons=reasons, samples=len(rows))
+        return res
+
+
+# ----------------------------------------------------------------------------- peaks, traffic
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("sm_max_mhz", 2070.0), "measured"
+    return 6800.0, 1900.0, 2070.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2406_09654_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel sources are unchanged."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(f"{kernel}@{workload}")
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ----------------------------------------------------------------------------- oracle baseline
+
+CPU_SNIPPET = r"""
+import sys, time, json, numpy as np
+sys.path.insert(0, {root!r})
+from oracle import coral_oracle as O
+from paper_2406_09654_gb300 import worlds
+w = worlds.make_world({workload!r}, seed={seed})
+st = O.State.from_world(w)
+p = O.Params.from_world(w)
+nets = O.nets_from_genomes(O.Genomes.from_genes(w.genes, w.n_genomes), w.hidden) if w.genes is not None \
+    else O.Nets.from_dense(w.dense, w.hidden)
+rows = {rows}
+budget = {budget}
+done = 0; spent = 0.0; bands = 0
+y = 0
+while (spent < budget or bands == 0) and y < w.height:
+    cells = np.arange(y * w.width, min(w.height, y + rows) * w.width)
+    t0 = time.perf_counter()
+    O.step_cells(st, nets, 0, p, cells)
+    spent += time.perf_counter() - t0
+    done += len(cells); bands += 1; y += rows
+print(json.dumps(dict(cells=done, seconds=spent, bands=bands)))
+"""
+
+
+def cpu_baseline(workload, seed, budget, rows=16):
+    """The FP64 oracle as it stands, one thread, on bands of `rows` full rows of the same world
+    (pass 1 on the band and its neighbours, pass 2 on the band) until about `budget` seconds."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    code = CPU_SNIPPET.format(root=ROOT, workload=workload, seed=seed, rows=rows, budget=budget)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
+    if r.returncode != 0:
+        return {"value": None, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                "sample": "failed: " + r.stderr[-300:]}
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return {"value": d["cells"] / d["seconds"], "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{d['bands']} bands of {rows} full rows ({d['cells']} cells) of the same world, "
+                      f"step 0, {d['seconds']:.1f} s, 1 thread (FP64 numpy oracle)"}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_coral(a, rank, world_size, local):
+    import torch
+
+    from paper_2406_09654_gb300 import build, coral, worlds
+
+    torch.cuda.set_device(local)
+    build.build()
+    w = worlds.make_world(a.workload, seed=rank)
+    stream = torch.cuda.current_stream()
+    path = a.path
+    if path == "auto":
+        path = "bf16" if coral.bf16_available() else "fp32"
+    pid = coral.BF16_GROUPED if path == "bf16" else coral.FP32_PERCELL
+    N = w.n_cells
+    sub = coral.substrate_for_world(w, pid, stream=stream)
+
+    # warm-up, then K timed steps bracketed by barrier + synchronize
+    sub.step(a.warmup)
+    torch.cuda.synchronize()
+    t_first = sub.get_step()
+    clocks = ClockSampler(local)
+    if rank == 0:
+        clocks.start()
+    barrier(world_size)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    step_ms, stage_ms = sub.step_timed(a.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world_size)
+    ck = clocks.stop() if rank == 0 else {}
+    total_ms = e0.elapsed_time(e1)
+    total_s = max_over_ranks(total_ms / 1e3, world_size)
+    value = N * a.steps * world_size / total_s
+    M = int(w.physics.get("radiation_every", 0))
+    n_rad = sum(1 for t in range(t_first, t_first + a.steps) if M and (t + 1) % M == 0)
+    launches = 3 * a.steps + 8 * n_rad
+
+    # dominant kernel: pass 1 (the network)
+    p1_ms = float(np.mean(stage_ms[:, 0]))
+    p2_ms = float(np.mean(stage_ms[:, 1]))
+    hbm, bf16_tf, sm_max, peak_kind = measured_peaks()
+    H = w.hidden
+    macs = (54 * H + 10 * H) if H else 540
+    if path == "bf16":
+        achieved = P1_BYTES * N / (p1_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "peak_kind": peak_kind,
+                "traffic": recorded_traffic("pass1_bf16", a.workload), "kernel": "pass1_bf16"}
+    else:
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
+        achieved = 2 * macs * N / (p1_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "peak_kind": "derived: SMs x 128 FP32 lanes x 2 x max SM clock",
+                "traffic": recorded_traffic("pass1_fp32", a.workload), "kernel": "pass1_fp32"}
+    step_roof = STATE_BYTES * 2 * N / (total_ms / a.steps / 1e3) / 1e9
+
+    # FP32 plain path on the same world (the comparison the metric names)
+    fp32 = None
+    if path == "bf16" and a.fp32_steps > 0:
+        sub32 = coral.substrate_for_world(w, coral.FP32_PERCELL, stream=stream)
+        sub32.step(2)
+        torch.cuda.synchronize()
+        s_ms, _ = sub32.step_timed(a.fp32_steps)
+        fp32 = N / (float(np.mean(s_ms)) / 1e3)
+        sub32.close()
+
+    # end to end through the C ABI with pinned host buffers: load, step, read back
+    e2e = None
+    if a.e2e_steps > 0:
+        nbytes = STATE_BYTES * N
+        host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        sub.read_channels(coral.CH_ALL, out=host)
+        hv = host.numpy()
+        E = hv[0:4 * N].view(np.float32)
+        I = hv[4 * N:8 * N].view(np.float32)
+        C = hv[8 * N:24 * N].view(np.float32)
+        G = hv[24 * N:28 * N].view(np.int32)
+        R = hv[28 * N:29 * N]
+        t = sub.get_step()
+        torch.cuda.synchronize()
+        barrier(world_size)
+        t0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            sub.load_state(E, I, C, G, R)
+            sub.set_step(t)
+            sub.step(1)
+            sub.read_channels(coral.CH_ALL, out=host)
+            t += 1
+        el = max_over_ranks(time.perf_counter() - t0, world_size)
+        e2e = {"value": N * a.e2e_steps * world_size / el, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    sub.close()
+
+    if rank != 0:
+        return None
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world_size,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype":
+            "bf16 network operands, f32 accumulation and state, f64 flow sums and totals" if path == "bf16"
+            else "f32 (f64 flow sums and totals)",
+        "data": "synthetic (seeded world generator; the paper has no dataset)",
+        "config": {"workload": f"{a.workload}: {WORKLOADS[a.workload]}", "path": path, "width": w.width,
+                   "height": w.height, "genomes": w.n_genomes, "hidden": w.hidden,
+                   "l2": "no flush: state 487 MB per buffer > 129 MB L2" if a.workload == "cfg3" else
+                   "state smaller than L2",
+                   "parallelism": f"independent worlds x{world_size}"},
+        "p50_step_ms": float(np.percentile(step_ms, 50)), "p99_step_ms": float(np.percentile(step_ms, 99)),
+        "stage_ms": {"pass1": p1_ms, "pass2": p2_ms, "rest": float(np.mean(stage_ms[:, 2]))},
+        "roofline": roof,
+        "step_hbm_frac": step_roof / hbm,
+        "fp32_plain_value": fp32,
+        "speedup_vs_fp32_plain": (value / world_size / fp32) if fp32 else None,
+        "clocks": {"sm_mhz": ck.get("sm_mhz"), "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons", [])},
+        "e2e": e2e,
+        "gpu_launches": launches,
+    }
+    return line
+
+
+def main():
+    a = parse()
+    rank, world_size, local = dist_setup(a.gpus)
+    if a.impl == "reference":
+        if rank == 0:
+            per = []
+            cb = None
+            for k in range(a.warmup + a.steps):
+                cb = cpu_baseline(a.workload, 0, 0.0)
+                if k >= a.warmup:
+                    per.append(cb)
+            cells = sum(int(c["sample"].split("(")[1].split()[0]) for c in per)
+            secs = sum(int(c["sample"].split("(")[1].split()[0]) / c["value"] for c in per)
+            v = cells / secs
+            print(json.dumps({
+                "impl": "reference", "metric": METRIC, "value": v, "unit": "cell-updates/s",
+                "n_gpus": world_size, "steps": a.steps, "warmup": a.warmup,
+                "ms_per_step": 1e3 * secs / len(per), "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"{a.workload}: {WORKLOADS[a.workload]}", "path": "oracle"},
+                "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+                                 "sample": "each step: one band of 16 full rows of the world through the FP64 oracle"},
+                "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            }))
+        return
+    cb = None
+    if rank == 0 and world_size == 1 and not a.no_cpu_baseline:
+        cb = cpu_baseline(a.workload, 0, a.cpu_seconds)       # before any GPU work (fresh process)
+    line = run_coral(a, rank, world_size, local)
+    if rank == 0:
+        line["cpu_baseline"] = cb
+        print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -163,6 +163,14 @@ int coral_cppn_generate_weights(coral_substrate* s, const int32_t* slots_or_null
 int coral_step(coral_substrate* s, int32_t n_steps);
 
 /*
+ * coral_step with CUDA-event timing (tracing): same work, same stream, plus events recorded
+ * around each stage. step_ms: [n_steps] device time of each step; stage_ms: [n_steps][3]
+ * time of pass 1 (sense + network + actuators), pass 2 (exploration, flow, day/night) and the
+ * rest (totals, radiation). Host arrays, either may be NULL. Synchronises.
+ */
+int coral_step_timed(coral_substrate* s, int32_t n_steps, float* step_ms, float* stage_ms);
+
+/*
  * Copies the planes selected by channel_mask (CORAL_CH_*) of the current state into dst,
  * packed plane after plane in increasing bit order: E, I, C0..C3 as float32 [N], G as int32
  * [N], R as uint8 [N]. dst_bytes must cover them all (else E_CAPACITY). Synchronises.

@@ -66,6 +66,7 @@ SIGNATURES = {
     "coral_genome_table_load": (ctypes.c_int, [_VP, _I32, _VP, _VP, ctypes.c_int]),
     "coral_cppn_generate_weights": (ctypes.c_int, [_VP, _VP, _I32]),
     "coral_step": (ctypes.c_int, [_VP, _I32]),
+    "coral_step_timed": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
     "coral_read_channels": (ctypes.c_int, [_VP, _U32, _VP, _SZ, ctypes.c_int]),
     "coral_read_stats": (ctypes.c_int, [_VP, _I64, _I32, ctypes.POINTER(Stats)]),
     "coral_read_perm": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -220,6 +221,13 @@ class Substrate:
     # -- stepping
     def step(self, n=1):
         _check(lib().coral_step(self.h, int(n)), self.h)
+
+    def step_timed(self, n=1):
+        """Steps with CUDA-event timing; returns (step_ms [n], stage_ms [n][3])."""
+        step_ms = np.empty(int(n), np.float32)
+        stage_ms = np.empty((int(n), 3), np.float32)
+        _check(lib().coral_step_timed(self.h, int(n), step_ms.ctypes.data, stage_ms.ctypes.data), self.h)
+        return step_ms, stage_ms
 
     def set_step(self, t):
         _check(lib().coral_set_step(self.h, int(t)), self.h)

@@ -325,50 +325,105 @@ int coral_cppn_generate_weights(coral_substrate* s, const int32_t* slots, int32_
   return CORAL_OK;
 }
 
-int coral_step(coral_substrate* s, int32_t n_steps) {
+}  // extern "C"
+
+namespace {
+
+// Enqueues one step; ev (4 events or NULL) is recorded before pass 1, after pass 1, after
+// pass 2 and after the totals / radiation.
+int enqueue_step(coral_substrate* s, cudaEvent_t* ev) {
+  StepArgs a = step_args(s);
+  if (ev) CK(s, cudaEventRecord(ev[0], s->stream));
+  if (s->p.path == CORAL_NET_BF16_GROUPED)
+    CK(s, launch_pass1_bf16(a, s->stream, s->grid1));
+  else
+    CK(s, launch_pass1_fp32(a, s->stream, s->grid1));
+  if (ev) CK(s, cudaEventRecord(ev[1], s->stream));
+  CK(s, launch_pass2(a, s->stream, s->grid2));
+  if (ev) CK(s, cudaEventRecord(ev[2], s->stream));
+  CK(s, launch_stats(a, s->grid1, s->grid2, s->t, s->ring, s->stream));
+  s->cur ^= 1;
+  if (s->p.radiation_every > 0 && (s->t + 1) % s->p.radiation_every == 0) {
+    RadiationArgs r = {};
+    r.W = s->W;
+    r.H = s->H;
+    r.N = s->N;
+    r.G = s->st[s->cur].G;
+    r.g = s->g;
+    r.thr_mut = s->p.thr_mut;
+    r.thr_merge = s->p.thr_merge;
+    r.sigma = s->p.sigma_mut;
+    r.world = s->p.world;
+    r.seed = s->p.seed;
+    r.step = (uint32_t)s->t;
+    r.count = s->count;
+    r.blockcnt = s->blockcnt;
+    r.blockoff = s->blockoff;
+    r.hits = s->hits;
+    r.hitbits = s->hitbits;
+    r.max_hits = s->cap;
+    r.freelist = s->freelist;
+    r.newslots = s->newslots;
+    r.counters = s->counters;
+    r.rec = s->ring + (s->t % kRing);
+    CK(s, launch_radiation(r, s->stream));
+  }
+  if (ev) CK(s, cudaEventRecord(ev[3], s->stream));
+  ++s->t;
+  return CORAL_OK;
+}
+
+int step_preconditions(coral_substrate* s, int32_t n_steps) {
   if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
   if (n_steps < 0) return fail(s, CORAL_E_INVALID, "n_steps must be >= 0");
   if (!s->genomes_loaded) return fail(s, CORAL_E_STATE, "no genome table loaded");
   if (s->p.radiation_every > 0 && !s->has_cppn)
     return fail(s, CORAL_E_STATE, "radiation needs CPPN genomes (direct nets cannot mutate)");
-  for (int i = 0; i < n_steps; ++i) {
-    StepArgs a = step_args(s);
-    if (s->p.path == CORAL_NET_BF16_GROUPED)
-      CK(s, launch_pass1_bf16(a, s->stream, s->grid1));
-    else
-      CK(s, launch_pass1_fp32(a, s->stream, s->grid1));
-    CK(s, launch_pass2(a, s->stream, s->grid2));
-    CK(s, launch_stats(a, s->grid1, s->grid2, s->t, s->ring, s->stream));
-    s->cur ^= 1;
-    if (s->p.radiation_every > 0 && (s->t + 1) % s->p.radiation_every == 0) {
-      RadiationArgs r = {};
-      r.W = s->W;
-      r.H = s->H;
-      r.N = s->N;
-      r.G = s->st[s->cur].G;
-      r.g = s->g;
-      r.thr_mut = s->p.thr_mut;
-      r.thr_merge = s->p.thr_merge;
-      r.sigma = s->p.sigma_mut;
-      r.world = s->p.world;
-      r.seed = s->p.seed;
-      r.step = (uint32_t)s->t;
-      r.count = s->count;
-      r.blockcnt = s->blockcnt;
-      r.blockoff = s->blockoff;
-      r.hits = s->hits;
-      r.hitbits = s->hitbits;
-      r.max_hits = s->cap;
-      r.freelist = s->freelist;
-      r.newslots = s->newslots;
-      r.counters = s->counters;
-      r.rec = s->ring + (s->t % kRing);
-      CK(s, launch_radiation(r, s->stream));
-    }
-    ++s->t;
-  }
   return CORAL_OK;
 }
+
+}  // namespace
+
+extern "C" int coral_step(coral_substrate* s, int32_t n_steps) {
+  int rc = step_preconditions(s, n_steps);
+  if (rc) return rc;
+  for (int i = 0; i < n_steps; ++i)
+    if ((rc = enqueue_step(s, nullptr)) != CORAL_OK) return rc;
+  return CORAL_OK;
+}
+
+extern "C" int coral_step_timed(coral_substrate* s, int32_t n_steps, float* step_ms, float* stage_ms) {
+  int rc = step_preconditions(s, n_steps);
+  if (rc) return rc;
+  std::vector<cudaEvent_t> ev;
+  try {
+    ev.resize(4 * (size_t)n_steps);
+  } catch (...) {
+    return fail(s, CORAL_E_OOM, "host allocation failed");
+  }
+  int made = 0;
+  for (; made < 4 * n_steps; ++made)
+    if (cudaEventCreate(&ev[made]) != cudaSuccess) break;
+  if (made < 4 * n_steps) rc = fail(s, CORAL_E_CUDA, "cudaEventCreate failed");
+  for (int i = 0; rc == CORAL_OK && i < n_steps; ++i) rc = enqueue_step(s, &ev[4 * i]);
+  if (rc == CORAL_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = fail(s, CORAL_E_CUDA, "sync failed");
+  for (int i = 0; rc == CORAL_OK && i < n_steps; ++i) {
+    float t0 = 0, t1 = 0, t2 = 0;
+    cudaEventElapsedTime(&t0, ev[4 * i], ev[4 * i + 1]);
+    cudaEventElapsedTime(&t1, ev[4 * i + 1], ev[4 * i + 2]);
+    cudaEventElapsedTime(&t2, ev[4 * i + 2], ev[4 * i + 3]);
+    if (step_ms) cudaEventElapsedTime(&step_ms[i], ev[4 * i], ev[4 * i + 3]);
+    if (stage_ms) {
+      stage_ms[3 * i] = t0;
+      stage_ms[3 * i + 1] = t1;
+      stage_ms[3 * i + 2] = t2;
+    }
+  }
+  for (int k = 0; k < made; ++k) cudaEventDestroy(ev[k]);
+  return rc;
+}
+
+extern "C" {
 
 int coral_read_channels(coral_substrate* s, uint32_t mask, void* dst, size_t dst_bytes, int on_device) {
   if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");

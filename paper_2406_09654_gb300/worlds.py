@@ -112,33 +112,64 @@ def zipf_counts(total: int, n: int, s: float) -> np.ndarray:
 
 
 def hilbert_d2xy(order: int, d: np.ndarray):
-    """Textbook Hilbert-curve index -> (x, y) on a 2^order square (vectorised)."""
-    n = 1 << order
-    x = np.zeros_like(d)
-    y = np.zeros_like(d)
-    t = d.copy()
-    s = 1
-    while s < n:
-        rx = 1 & (t // 2)
-        ry = 1 & (t ^ rx)
+    """Textbook Hilbert-curve index -> (x, y) on a 2^order square (vectorised): at level s
+    (1, 2, 4, ...) take the next two bits (rx, ry) of d; when ry = 0 reflect (if rx = 1) and
+    transpose the coordinates gathered so far; then add s*rx, s*ry."""
+    t = np.asarray(d, np.int64).copy()
+    x = np.zeros(t.shape, np.int64)
+    y = np.zeros(t.shape, np.int64)
+    for level in range(order):
+        s = 1 << level
+        rx = (t >> 1) & 1
+        ry = (t ^ rx) & 1
         swap = ry == 0
         flip = swap & (rx == 1)
-        x = np.where(flip, s - 1 - x, x)
-        y = np.where(flip, s - 1 - y, y)
-        x, y = np.where(swap, y, x), np.where(swap, x, y)
-        x = x + s * rx
-        y = y + s * ry
-        t = t // 4
-        s *= 2
+        xf = np.where(flip, s - 1 - x, x)
+        yf = np.where(flip, s - 1 - y, y)
+        x = np.where(swap, yf, xf) + s * rx
+        y = np.where(swap, xf, yf) + s * ry
+        t >>= 2
     return x, y
+
+
+def hilbert_curve(order: int):
+    """(x, y) of every index 0 .. 4^order - 1 of the Hilbert curve, computed as the low
+    half-order curve (a table) carried through the high levels, whose reflections and
+    transpositions act on the low coordinates as one affine map per high index."""
+    lo = order // 2
+    hi_levels = order - lo
+    ux, uy = hilbert_d2xy(lo, np.arange(1 << (2 * lo)))          # low table
+    hi = np.arange(1 << (2 * hi_levels), dtype=np.int64)
+    # x = fx * (swapped ? uy : ux) + ox,  y = fy * (swapped ? ux : uy) + oy
+    swapped = np.zeros(hi.shape, bool)
+    fx = np.ones(hi.shape, np.int64); fy = np.ones(hi.shape, np.int64)
+    ox = np.zeros(hi.shape, np.int64); oy = np.zeros(hi.shape, np.int64)
+    t = hi.copy()
+    for level in range(lo, order):
+        s = 1 << level
+        rx = (t >> 1) & 1
+        ry = (t ^ rx) & 1
+        swap = ry == 0
+        flip = swap & (rx == 1)
+        fx = np.where(flip, -fx, fx); ox = np.where(flip, s - 1 - ox, ox)
+        fy = np.where(flip, -fy, fy); oy = np.where(flip, s - 1 - oy, oy)
+        swapped = swapped ^ swap
+        fx, fy = np.where(swap, fy, fx), np.where(swap, fx, fy)
+        ox, oy = np.where(swap, oy, ox), np.where(swap, ox, oy)
+        ox = ox + s * rx
+        oy = oy + s * ry
+        t >>= 2
+    sw = swapped[:, None]
+    x = fx[:, None] * np.where(sw, uy[None, :], ux[None, :]) + ox[:, None]
+    y = fy[:, None] * np.where(sw, ux[None, :], uy[None, :]) + oy[:, None]
+    return x.ravel(), y.ravel()
 
 
 def _hilbert_zipf(width, height, n, s):
     """Genome k owns the k-th contiguous run of a Hilbert curve, run lengths Zipf(s)."""
     order = max(1, int(np.ceil(np.log2(max(width, height)))))
     side = 1 << order
-    d = np.arange(side * side, dtype=np.int64)
-    x, y = hilbert_d2xy(order, d)
+    x, y = hilbert_curve(order)
     keep = (x < width) & (y < height)
     x, y = x[keep], y[keep]
     counts = zipf_counts(width * height, n, s)

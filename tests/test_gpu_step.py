@@ -55,9 +55,13 @@ def test_cfg1_fp32_forced_100_steps():
     print("cfg1 worst per-channel error", worst, "band cells", banded)
 
 
+FREE_TAU = 2e-6   # about 5x the FP32 path's observed per-step error on cfg1
+
+
 def test_cfg1_fp32_free_running_100_steps():
-    """Free-running: both sides step from the initial state with no re-loading; reports the
-    first step (if any) at which the oracle met a near-tie and stops comparing there."""
+    """Free-running: both sides step from the initial state with no re-loading. Compared
+    step by step until the oracle meets a decision within FREE_TAU of flipping (then the
+    trajectories may legitimately part); the step reached is printed."""
     w = worlds.make_world("cfg1", seed=0)
     st, nets, gen, p = oracle_setup(w)
     sub = coral.substrate_for_world(w, coral.FP32_PERCELL)
@@ -66,7 +70,7 @@ def test_cfg1_fp32_free_running_100_steps():
         for t in range(100):
             new, info = O.step(st, nets, t, p)
             sub.step(1)
-            mask = band_mask(st, info, FP32_TAU)
+            mask = band_mask(st, info, FREE_TAU)
             if mask.any():
                 first_band = t
                 break
@@ -77,7 +81,9 @@ def test_cfg1_fp32_free_running_100_steps():
             st = new
     finally:
         sub.close()
-    print("first step with a near-tie:", first_band)
+    print("free-running cfg1: identical within tolerance up to step",
+          100 if first_band is None else first_band)
+    assert first_band is None or first_band >= 5
 
 
 @pytest.mark.parametrize("W,H,n,hidden,rot", [(3, 3, 1, 0, 1), (3, 5, 2, 16, 1), (37, 29, 7, 32, 1),
