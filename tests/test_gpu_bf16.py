@@ -1,0 +1,94 @@
+"""GPU parity of the BF16 tensor-core (tcgen05) network path against the oracle.
+
+Two references:
+  * the FP64 oracle (exact network) — the stated contract: per-channel normwise error <= 2e-2,
+    decisions compared outside a 3e-2 band;
+  * the oracle with BF16 network operands (x, W1 with b1, h, W2 rounded to bfloat16, exact
+    sums) — the arithmetic the tensor-core path defines; what remains is FP32 accumulation
+    order and the hardware tanh (relative error below 2^-10.9), so the tolerance is 3e-3 and
+    the decision band 5e-3.
+"""
+import numpy as np
+import pytest
+
+from oracle import coral_oracle as O
+from paper_2406_09654_gb300 import coral, worlds
+from parity import (BF16_TAU, BF16_TOL, band_mask, compare_step, oracle_setup, round32,
+                    state_arrays)
+
+pytestmark = pytest.mark.gpu
+
+BF16_OP_TOL = 3e-3
+BF16_OP_TAU = 5e-3
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2406_09654_gb300 import build
+    build.build()
+    coral.lib()
+    assert coral.bf16_available(), "the tcgen05 path must be available on this GPU"
+
+
+def forced(world, steps, tol, tau, t0=0, net_precision="fp64", max_band_frac=None):
+    st, nets, gen, p = oracle_setup(world, net_precision=net_precision)
+    sub = coral.substrate_for_world(world, coral.BF16_GROUPED)
+    worst, band = {}, 0
+    try:
+        st = round32(st)
+        for t in range(t0, t0 + steps):
+            sub.load_state(*state_arrays(st))
+            sub.set_step(t)
+            sub.step(1)
+            g = sub.read_channels()
+            new, info = O.step(st, nets, t, p)
+            mask = band_mask(st, info, tau)
+            band += int(mask.sum())
+            errs, bad_G, bad_R = compare_step(g, new, mask, tol)
+            assert bad_G == 0 and bad_R == 0, (t, bad_G, bad_R)
+            for k, v in errs.items():
+                worst[k] = max(worst.get(k, 0.0), v)
+            assert max(errs.values()) <= tol, (t, errs)
+            st = round32(new)
+    finally:
+        sub.close()
+    if max_band_frac is not None:
+        assert band <= max_band_frac * steps * world.n_cells
+    return worst, band
+
+
+@pytest.mark.parametrize("W,H,n,hidden,layout", [(64, 64, 8, 0, "voronoi"), (96, 40, 6, 32, "voronoi"),
+                                                 (37, 29, 5, 64, "voronoi"), (33, 7, 3, 16, "voronoi"),
+                                                 (64, 64, 9, 48, "voronoi"), (40, 24, 50, 64, "random")])
+def test_bf16_matches_bf16_operand_oracle(W, H, n, hidden, layout):
+    w = worlds.make_world(width=W, height=H, n_genomes=n, hidden=hidden, layout=layout,
+                          net="cppn" if hidden else "direct", seed=W + H + hidden, random_rotation=True)
+    worst, band = forced(w, 3, BF16_OP_TOL, BF16_OP_TAU, t0=98, net_precision="bf16", max_band_frac=0.05)
+    print(W, H, hidden, layout, "worst", worst, "band cells", band)
+
+
+@pytest.mark.parametrize("hidden", [0, 32, 64])
+def test_bf16_within_stated_tolerance_of_fp64_oracle(hidden):
+    w = worlds.make_world(width=128, height=96, n_genomes=12, hidden=hidden,
+                          net="cppn" if hidden else "direct", seed=5 + hidden)
+    worst, band = forced(w, 3, BF16_TOL, BF16_TAU)
+    print("hidden", hidden, "worst per-channel error vs FP64 oracle", worst, "band cells", band)
+
+
+def test_bf16_minimum_torus_and_single_genome():
+    w = worlds.make_world(width=3, height=3, n_genomes=1, hidden=64, net="cppn", seed=1)
+    forced(w, 2, BF16_OP_TOL, BF16_OP_TAU, net_precision="bf16")
+
+
+def test_bf16_radiation_and_determinism():
+    w = worlds.make_world(width=160, height=96, n_genomes=20, hidden=64, net="cppn", seed=4,
+                          radiation_every=3, p_mut=2e-3, p_merge=2e-3, capacity=600)
+    outs = []
+    for _ in range(2):
+        with coral.substrate_for_world(w, coral.BF16_GROUPED) as sub:
+            sub.step(10)
+            outs.append(sub.read_channels())
+            s = sub.read_stats(8, 1)[0]
+            assert s["n_born"] > 0 and s["n_live"] > 20
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
