@@ -28,8 +28,11 @@ numbered reading [R1]..[R16]; each function names the readings it follows. The r
 [R4]  communication: C' = sigmoid(a_k / max(1, ||a_0..3||_2)).
 [R5]  invest i = k_inv max(a4,0), liquidate l = k_liq max(a5,0);
       E1 = E - iE + lI, I1 = I + iE - lI.
-[R6]  exploration: k* = argmax a6..a9 (first on ties), m = its value; explore iff m > 0 and
-      I1 > 0 with x = k_exp m I1 toward d = (R + [0,1,3,2][k*]) mod 4; the explorer loses x,
+[R6]  exploration: k* = the maximal explore actuator (first on ties), m = its value; explore
+      iff m > 0 and I1 > 0 with x = k_exp m I1 toward d = (R + [0,1,3,2][k*]) mod 4. The
+      actuator is picked and m > 0 tested on the pre-activations z6..z9 (tanh is strictly
+      increasing, so it is the same actuator and the same sign; comparing z avoids ties made
+      by rounding saturated tanh outputs to 1). The explorer loses x,
       the target absorbs every incoming x; the largest incoming x wins (ties N,E,S,W) and
       takes the target over iff x > I1(target): target adopts the explorer's genome and
       rotation d.
@@ -233,8 +236,8 @@ def round_bf16(a):
 
 
 def network(x, genome, nets: Nets, p: Params):
-    """a = tanh(W x + b) (hidden = 0) or a = tanh(W2 tanh(W1 x + b1) + b2) [R9], with the
-    weights of each cell's genome slot."""
+    """Output pre-activations z = W x + b (hidden = 0) or z = W2 tanh(W1 x + b1) + b2, with
+    the weights of each cell's genome slot; the actuators are a = tanh(z) [R9]."""
     a = np.empty((len(x), N_OUT))
     bf = p.net_precision == "bf16"
     xin = round_bf16(x) if bf else x
@@ -245,13 +248,13 @@ def network(x, genome, nets: Nets, p: Params):
             W1, b1 = round_bf16(W1), round_bf16(b1)
         z = xin[rows] @ W1.T + b1
         if nets.hidden == 0:
-            a[rows] = np.tanh(z)
+            a[rows] = z
             continue
         h = np.tanh(z)
         W2 = nets.W2[g]
         if bf:
             h, W2 = round_bf16(h), round_bf16(W2)
-        a[rows] = np.tanh(h @ W2.T + nets.b2[g])
+        a[rows] = h @ W2.T + nets.b2[g]
     return a
 
 
@@ -275,22 +278,23 @@ def invest_liquidate(E, I, a, p: Params):
     return E1, I1
 
 
-def explore_decision(a, I1, R, p: Params):
+def explore_decision(z, a, I1, R, p: Params):
     """[R6] pick the maximal explore actuator; explore iff it is positive and I1 > 0.
-    Returns (direction 0..3 or -1, amount, margin). The decision compares float32 values
-    [R14]; the margin is the smaller of (top1 - top2) and |top1| in FP64."""
-    logits = a[:, 6:10]
+    z, a: pre-activations and actuators. Returns (direction 0..3 or -1, amount, margin). The
+    decision compares float32 values [R14]; the margin is the smaller of (top1 - top2) and
+    |top1| of the pre-activations in FP64."""
+    logits = z[:, 6:10]
     l32 = logits.astype(np.float32)
     k = np.argmax(l32, axis=1)                       # first maximum
-    m32 = l32[np.arange(len(a)), k]
-    m = logits[np.arange(len(a)), k]
+    m32 = l32[np.arange(len(z)), k]
+    m = a[np.arange(len(a)), 6 + k]
     go = (m32 > 0) & (I1.astype(np.float32) > 0)
     turn = np.asarray(EXPLORE_TURN)[k]
     Rv = R if p.rotation else np.zeros_like(R)
     d = np.where(go, (Rv + turn) % 4, -1)
     amt = np.where(go, p.k_exp * m * I1, 0.0)
     srt = np.sort(logits, axis=1)
-    margin = np.minimum(srt[:, 3] - srt[:, 2], np.abs(m))
+    margin = np.minimum(srt[:, 3] - srt[:, 2], np.abs(srt[:, 3]))
     margin = np.where(I1 > 0, margin, np.inf)
     return d.astype(np.int64), amt, margin
 
@@ -312,13 +316,14 @@ def pass1(st: State, nets: Nets, cells, p: Params):
     n = st.n
     cells = np.asarray(cells, np.int64)
     x = sense(st, cells, p)
-    a = network(x, st.G[cells], nets, p)
+    z = network(x, st.G[cells], nets, p)
+    a = np.tanh(z)
     out = {k: np.full(n, np.nan) for k in ("E1", "I1", "amt", "S", "margin")}
     out["dir"] = np.full(n, -2, np.int64)
     out["C"] = np.full((4, n), np.nan)
     out["a"] = np.full((n, N_OUT), np.nan)
     E1, I1 = invest_liquidate(st.E[cells], st.I[cells], a, p)
-    d, amt, margin = explore_decision(a, I1, st.R[cells], p)
+    d, amt, margin = explore_decision(z, a, I1, st.R[cells], p)
     out["E1"][cells], out["I1"][cells] = E1, I1
     out["dir"][cells], out["amt"][cells], out["margin"][cells] = d, amt, margin
     out["S"][cells] = flow_denominator(st, cells)

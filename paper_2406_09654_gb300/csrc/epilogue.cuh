@@ -12,10 +12,12 @@ struct CellOut {
   uint8_t xdir;
 };
 
-// a[0..3] com, a[4] invest, a[5] liquidate, a[6..9] explore (fwd, right, left, back).
+// a[0..3] com, a[4] invest, a[5] liquidate, a[6..9] explore (fwd, right, left, back);
+// z[6..9]: pre-activations of the explore actuators (tanh is strictly increasing, so the
+// maximal actuator and its sign are read off z, where saturated outputs cannot tie).
 // E, I: the cell's state; S: FP64 sum of I_t over its 4 von Neumann neighbours; r: rotation.
-__device__ __forceinline__ void actuator_epilogue(const StepArgs& p, const float* a, float E,
-                                                  float I, double S, int r, CellOut& o) {
+__device__ __forceinline__ void actuator_epilogue(const StepArgs& p, const float* a, const float* z,
+                                                  float E, float I, double S, int r, CellOut& o) {
   // Communication: normalised by max(1, ||a0..3||) and passed through a sigmoid.
   const float n2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3];
   const float nrm = fmaxf(1.0f, sqrtf(n2));
@@ -28,11 +30,12 @@ __device__ __forceinline__ void actuator_epilogue(const StepArgs& p, const float
   const float I1 = I + inv * E - liq * I;
   // Exploration toward the maximal explore actuator (first maximum on ties).
   int k = 0;
-  float m = a[6];
-  if (a[7] > m) { k = 1; m = a[7]; }
-  if (a[8] > m) { k = 2; m = a[8]; }
-  if (a[9] > m) { k = 3; m = a[9]; }
-  const bool go = (m > 0.0f) && (I1 > 0.0f);
+  float zm = z[6];
+  if (z[7] > zm) { k = 1; zm = z[7]; }
+  if (z[8] > zm) { k = 2; zm = z[8]; }
+  if (z[9] > zm) { k = 3; zm = z[9]; }
+  const float m = a[6 + k];
+  const bool go = (zm > 0.0f) && (I1 > 0.0f);
   o.xdir = go ? (uint8_t)((r + explore_turn(k)) & 3) : kNoExplore;
   o.xamt = go ? p.k_exp * m * I1 : 0.0f;
   o.I1 = I1;

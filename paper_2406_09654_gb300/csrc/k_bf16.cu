@@ -140,9 +140,9 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
     }
     // 4. one tensor-core round per genome present in the tile
     bool done = g < 0;
-    float act[kOut];
+    float act[kOut], zo[kOut];
 #pragma unroll
-    for (int o = 0; o < kOut; ++o) act[o] = 0.0f;
+    for (int o = 0; o < kOut; ++o) act[o] = zo[o] = 0.0f;
     while (true) {
       const unsigned b = __ballot_sync(0xffffffffu, !done);
       if (lane == 0) ballots[warp] = b;
@@ -184,7 +184,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
         tc::tmem_wait_ld();
         if (mine) {
 #pragma unroll
-          for (int o = 0; o < kOut; ++o) act[o] = tc::tanh_approx(v[o]);
+          for (int o = 0; o < kOut; ++o) {
+            zo[o] = v[o];
+            act[o] = tc::tanh_approx(v[o]);
+          }
         }
       } else {
         const uint32_t row2 = base_s + kOffA2 + tid * 128;
@@ -219,7 +222,10 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
         if (mine) {
           const float* b2 = reinterpret_cast<const float*>(base + kOffW + bf16_b2_off(H));
 #pragma unroll
-          for (int o = 0; o < kOut; ++o) act[o] = tc::tanh_approx(v[o] + b2[o]);
+          for (int o = 0; o < kOut; ++o) {
+            zo[o] = v[o] + b2[o];
+            act[o] = tc::tanh_approx(zo[o]);
+          }
         }
       }
       tc::tc_fence_before();
@@ -233,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
     if (valid) {
       const float* sI = stage + kHaloCells;
       const double S = (double)sI[hc - kHaloW] + (double)sI[hc + 1] + (double)sI[hc + kHaloW] + (double)sI[hc - 1];
-      actuator_epilogue(a, act, stage[hc], sI[hc], S, r, o);
+      actuator_epilogue(a, act, zo, stage[hc], sI[hc], S, r, o);
       store_pass1(a, j, o);
     }
 #pragma unroll

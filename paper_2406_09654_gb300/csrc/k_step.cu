@@ -73,7 +73,7 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1_fp32(const StepArgs a) {
         load6(a.cur, n, N, in + 6 * p);
       }
       const float* net = a.nets32 + (long long)a.cur.G[j] * a.net_stride;
-      float act[kOut];
+      float act[kOut], zo[kOut];
       if (a.hidden == 0) {
 #pragma unroll
         for (int oo = 0; oo < kOut; ++oo) {
@@ -90,6 +90,7 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1_fp32(const StepArgs a) {
           const float4 w4 = __ldg(w + 13);
           acc = fmaf(w4.x, in[52], acc);
           acc = fmaf(w4.y, in[53], acc);
+          zo[oo] = acc;
           act[oo] = tanhf(acc);
         }
       } else {
@@ -129,11 +130,14 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1_fp32(const StepArgs a) {
           acc2[9] = fmaf(u2.y, h, acc2[9]);
         }
 #pragma unroll
-        for (int oo = 0; oo < kOut; ++oo) act[oo] = tanhf(acc2[oo]);
+        for (int oo = 0; oo < kOut; ++oo) {
+          zo[oo] = acc2[oo];
+          act[oo] = tanhf(acc2[oo]);
+        }
       }
       // FP64 flow denominator: I_t of the von Neumann neighbours (kernel ranks 1, 4, 5, 8).
       const double S = (double)in[7] + (double)in[25] + (double)in[31] + (double)in[49];
-      actuator_epilogue(a, act, in[0], in[1], S, r, o);
+      actuator_epilogue(a, act, zo, in[0], in[1], S, r, o);
       store_pass1(a, j, o);
     }
 #pragma unroll

@@ -136,10 +136,10 @@ def test_sense_rotation_symmetry():
 
 # ----------------------------------------------------------------------------- network
 
-def test_network_zero_weights_gives_tanh_bias():
+def test_network_zero_weights_gives_bias():
     nets = O.Nets(0, np.zeros((1, 10, 54)), np.linspace(-2, 2, 10)[None])
-    a = O.network(np.random.default_rng(0).normal(size=(7, 54)), np.zeros(7, np.int64), nets, O.Params())
-    assert np.allclose(a, np.tanh(np.linspace(-2, 2, 10))[None], rtol=0, atol=1e-15)
+    z = O.network(np.random.default_rng(0).normal(size=(7, 54)), np.zeros(7, np.int64), nets, O.Params())
+    assert np.array_equal(z, np.broadcast_to(np.linspace(-2, 2, 10)[None], (7, 10)))
 
 
 def test_network_orientation_single_connection():
@@ -147,9 +147,9 @@ def test_network_orientation_single_connection():
     W = np.zeros((1, 10, 54)); W[0, 3, 17] = 0.7
     nets = O.Nets(0, W, np.zeros((1, 10)))
     x = np.zeros((2, 54)); x[0, 17] = 1.0; x[1, 3] = 1.0
-    a = O.network(x, np.zeros(2, np.int64), nets, O.Params())
-    assert a[0, 3] == pytest.approx(math.tanh(0.7), abs=1e-15)
-    assert np.count_nonzero(a) == 1
+    z = O.network(x, np.zeros(2, np.int64), nets, O.Params())
+    assert z[0, 3] == pytest.approx(0.7, abs=1e-15)
+    assert np.count_nonzero(z) == 1
 
 
 def test_network_two_layer_brute_force():
@@ -163,7 +163,7 @@ def test_network_two_layer_brute_force():
         h = [math.tanh(sum(nets.W1[g[c], k, i] * x[c, i] for i in range(54)) + nets.b1[g[c], k])
              for k in range(H)]
         for o in range(10):
-            ref = math.tanh(sum(nets.W2[g[c], o, k] * h[k] for k in range(H)) + nets.b2[g[c], o])
+            ref = sum(nets.W2[g[c], o, k] * h[k] for k in range(H)) + nets.b2[g[c], o]
             assert a[c, o] == pytest.approx(ref, rel=1e-13, abs=1e-14)
 
 
@@ -205,7 +205,7 @@ def test_invest_liquidate_hand_values():
 # ----------------------------------------------------------------------------- hand-built steps
 
 def const_nets(biases):
-    """Direct nets with zero weights: genome g outputs exactly tanh(biases[g])."""
+    """Direct nets with zero weights: genome g's actuators are exactly tanh(biases[g])."""
     b = np.asarray(biases, np.float64)
     return O.Nets(0, np.zeros((len(b), 10, 54)), b)
 
@@ -544,3 +544,14 @@ def test_step_cells_equals_full_step():
     assert np.allclose(o["I"], full.I[cells], rtol=1e-14, atol=0)
     assert np.array_equal(o["G"], full.G[cells]) and np.array_equal(o["R"], full.R[cells])
     assert np.allclose(o["C"], full.C[:, cells], rtol=1e-14, atol=0)
+
+
+def test_explore_argmax_on_preactivations_breaks_saturated_ties():
+    # actuators 7 and 8 both round to 1.0 in float32 but their pre-activations differ: the
+    # maximal actuator is the one with the larger pre-activation
+    z = np.zeros((1, 10)); z[0, 6:10] = [-1.0, 12.0, 13.0, 0.5]
+    a = np.tanh(z)
+    assert a.astype(np.float32)[0, 7] == a.astype(np.float32)[0, 8] == 1.0
+    d, amt, margin = O.explore_decision(z, a, np.array([1.0]), np.array([0]), O.Params())
+    assert d[0] == 3 and margin[0] == pytest.approx(1.0)          # logit k=2 -> left of north
+    assert amt[0] == pytest.approx(0.5 * math.tanh(13.0))
