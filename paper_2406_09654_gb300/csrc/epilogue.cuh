@@ -30,11 +30,10 @@ __device__ __forceinline__ void actuator_epilogue(const StepArgs& p, const float
   const float I1 = I + inv * E - liq * I;
   // Exploration toward the maximal explore actuator (first maximum on ties).
   int k = 0;
-  float zm = z[6];
-  if (z[7] > zm) { k = 1; zm = z[7]; }
-  if (z[8] > zm) { k = 2; zm = z[8]; }
-  if (z[9] > zm) { k = 3; zm = z[9]; }
-  const float m = a[6 + k];
+  float zm = z[6], m = a[6];
+  if (z[7] > zm) { k = 1; zm = z[7]; m = a[7]; }
+  if (z[8] > zm) { k = 2; zm = z[8]; m = a[8]; }
+  if (z[9] > zm) { k = 3; zm = z[9]; m = a[9]; }
   const bool go = (zm > 0.0f) && (I1 > 0.0f);
   o.xdir = go ? (uint8_t)((r + explore_turn(k)) & 3) : kNoExplore;
   o.xamt = go ? p.k_exp * m * I1 : 0.0f;

@@ -1,10 +1,12 @@
-// BF16 tensor-core network (pass 1) on tcgen05: each CTA takes 32x4-cell tiles of the torus,
-// stages the tile plus a one-cell halo of the six sensor channels in shared memory, builds the
+// BF16 tensor-core network (pass 1) on tcgen05: each CTA takes a contiguous run of 32x4-cell
+// tiles of the torus, prefetches the next tile's one-cell halo of the six sensor channels into
+// shared memory with cp.async while it works on the current one, builds the
 // 128 x 64 BF16 input tile (the rotation-ordered 3x3 neighbourhood of every cell, K index
 // 6*rank + channel, a constant 1 at K = 54 that carries the layer-1 bias), and runs the genome
 // nets on the tensor cores with FP32 accumulation in TMEM: one 128 x H x 64 MMA for layer 1,
-// tanh in the epilogue, one 128 x 16 x H MMA for layer 2. A tile with several genomes runs one
-// round per genome (the rows of other genomes are computed and discarded). The actuator
+// tanh in the epilogue (the hidden tile overwrites the consumed input tile, layer 2 reuses the
+// TMEM columns), one 128 x 16 x H MMA for layer 2. A tile with several genomes runs one round per
+// genome (the rows of other genomes are computed and discarded). The actuator
 // epilogue (communication, invest/liquidate, exploration, flow quotient) follows in registers.
 #include <math.h>
 
@@ -17,19 +19,21 @@ namespace coral {
 namespace {
 
 constexpr int kThreads = 128;
+constexpr int kCtasPerSm = 5;
 constexpr int kTileW = 32, kTileH = 4;
 constexpr int kHaloW = kTileW + 2, kHaloH = kTileH + 2;
 constexpr int kHaloCells = kHaloW * kHaloH;               // 204
-constexpr uint32_t kTmemCols = 128;
-constexpr uint32_t kL2Col = 64;                           // TMEM column of the layer-2 accumulator
+constexpr int kStageFloats = 6 * kHaloCells;              // 1224
+constexpr int kLoadsPerThread = (kStageFloats + kThreads - 1) / kThreads;
+constexpr uint32_t kTmemCols = 64;                        // layer 1, then layer 2 in cols 0..15
 constexpr long long kWaitCycles = 4000000000LL;           // about 2 s of SM clock
 
 // shared memory layout, offsets from a 1024-byte aligned base
-constexpr int kOffA = 0;                                  // 128 rows x 128 B input tile
-constexpr int kOffA2 = 16384;                             // 128 rows x 128 B hidden tile
-constexpr int kOffW = 32768;                              // genome blob (<= 10368 B)
-constexpr int kOffStage = kOffW + 11264;                  // float32 [6][204]
-constexpr int kOffRec = kOffStage + 4928;                 // 204 x 16 B BF16 cell records
+constexpr int kOffA = 0;                                  // 128 x 128 B: input tile, then hidden tile
+constexpr int kOffW = 16384;                              // genome blob (<= 10368 B)
+constexpr int kStageBytes = 4928;                         // float32 [6][204], two buffers
+constexpr int kOffStage = kOffW + 11264;
+constexpr int kOffRec = kOffStage + 2 * kStageBytes;      // 204 x 16 B BF16 cell records
 constexpr int kOffG = kOffRec + kHaloCells * 16;          // int32 [128]
 constexpr int kOffMisc = kOffG + 512;                     // mbarrier, TMEM slot, flags
 constexpr int kSmemBytes = kOffMisc + 128 + 1024;         // + alignment slack
@@ -39,12 +43,29 @@ __device__ __forceinline__ int modp(int v, int n) {
   return v < 0 ? v + n : v;
 }
 
-__global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
+// Starts the asynchronous copy of a tile's 34 x 6 halo of the six sensor planes (wrap-around)
+// into a stage buffer; one commit group per call.
+__device__ __forceinline__ void issue_halo(const StepArgs& a, long long tile, int tiles_x, uint32_t dst) {
+  const int x0 = (int)(tile % tiles_x) * kTileW, y0 = (int)(tile / tiles_x) * kTileH;
+#pragma unroll
+  for (int k = 0; k < kLoadsPerThread; ++k) {
+    const int i = threadIdx.x + k * kThreads;
+    if (i < kStageFloats) {
+      const int ch = i / kHaloCells, c = i - ch * kHaloCells;
+      const int hy = c / kHaloW, hx = c - hy * kHaloW;
+      const long long n = (long long)modp(y0 - 1 + hy, a.H) * a.W + modp(x0 - 1 + hx, a.W);
+      const float* plane = ch == 0 ? a.cur.E : (ch == 1 ? a.cur.I : a.cur.C + (long long)(ch - 2) * a.N);
+      tc::cp_async4(dst + 4 * i, plane + n);
+    }
+  }
+  tc::cp_async_commit();
+}
+
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepArgs a) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_s = tc::smem_u32(smem_raw);
   const uint32_t base_s = (raw_s + 1023u) & ~1023u;
   uint8_t* base = smem_raw + (base_s - raw_s);
-  float* stage = reinterpret_cast<float*>(base + kOffStage);
   int32_t* sG = reinterpret_cast<int32_t*>(base + kOffG);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(base + kOffMisc);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + kOffMisc + 8);
@@ -56,11 +77,11 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int W = a.W, Hh = a.H;
-  const long long N = a.N;
   const int H = a.hidden;
   const int N1 = H ? H : 16;
   const uint32_t rec_s = base_s + kOffRec;
   const uint32_t w_s = base_s + kOffW;
+  const uint32_t a_s = base_s + kOffA;
 
   if (warp == 0) {
     tc::tmem_alloc(tmem_slot, kTmemCols);
@@ -85,17 +106,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
   bool timed_out = false;
   const int tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (Hh + kTileH - 1) / kTileH;
   const long long n_tiles = (long long)tiles_x * tiles_y;
+  // a contiguous run of tiles per CTA: neighbouring tiles share halo rows (L2) and genomes
+  const long long per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const long long t_begin = (long long)blockIdx.x * per;
+  const long long t_end = t_begin + per < n_tiles ? t_begin + per : n_tiles;
+  if (t_begin < t_end) issue_halo(a, t_begin, tiles_x, base_s + kOffStage);
 
-  for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+  int buf = 0;
+  for (long long tile = t_begin; tile < t_end; ++tile, buf ^= 1) {
     const int x0 = (int)(tile % tiles_x) * kTileW, y0 = (int)(tile / tiles_x) * kTileH;
-    // 1. tile + halo of the six sensor channels, float32, wrap-around
-    for (int i = tid; i < 6 * kHaloCells; i += kThreads) {
-      const int ch = i / kHaloCells, c = i - ch * kHaloCells;
-      const int hy = c / kHaloW, hx = c - hy * kHaloW;
-      const long long n = (long long)modp(y0 - 1 + hy, Hh) * W + modp(x0 - 1 + hx, W);
-      const float* plane = ch == 0 ? a.cur.E : (ch == 1 ? a.cur.I : a.cur.C + (long long)(ch - 2) * N);
-      stage[i] = __ldg(plane + n);
-    }
     const int gx = x0 + lane, gy = y0 + warp;
     const bool valid = gx < W && gy < Hh;
     const long long j = (long long)gy * W + gx;
@@ -104,9 +123,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
       g = __ldg(a.cur.G + j);
       r = a.rotation ? (int)__ldg(a.cur.R + j) : 0;
     }
+    tc::cp_async_wait_all();
     sG[tid] = g;
-    __syncthreads();
-    // 2. BF16 records: 6 channels of each halo cell in one 16-byte slot
+    __syncthreads();                                  // this tile's halo is in stage[buf]
+    if (tile + 1 < t_end) issue_halo(a, tile + 1, tiles_x, base_s + kOffStage + (buf ^ 1) * kStageBytes);
+    const float* stage = reinterpret_cast<const float*>(base + kOffStage + buf * kStageBytes);
+    // BF16 records: the 6 channels of each halo cell in one 16-byte slot
     for (int c = tid; c < kHaloCells; c += kThreads) {
       const float* s = stage + c;
       tc::sts128(rec_s + c * 16, tc::pack_bf16x2(s[0], s[kHaloCells]),
@@ -114,35 +136,13 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
                  tc::pack_bf16x2(s[4 * kHaloCells], s[5 * kHaloCells]), 0u);
     }
     __syncthreads();
-    // 3. this cell's input row: 9 records in kernel-rank order, 1.0 at K = 54, swizzled
     const int hc = (warp + 1) * kHaloW + (lane + 1);
-    {
-      uint32_t wv[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) wv[i] = 0u;
-      if (valid) {
-        uint4 rc = tc::lds128(rec_s + hc * 16);
-        wv[0] = rc.x; wv[1] = rc.y; wv[2] = rc.z;
-#pragma unroll
-        for (int p = 1; p < 9; ++p) {
-          int dx, dy;
-          octant_offset((2 * r + rank_delta(p)) & 7, dx, dy);
-          rc = tc::lds128(rec_s + (hc + dy * kHaloW + dx) * 16);
-          wv[3 * p] = rc.x; wv[3 * p + 1] = rc.y; wv[3 * p + 2] = rc.z;
-        }
-        wv[27] = 0x3F80u;                    // bf16 1.0 at K = 54 (layer-1 bias), 0 at K = 55
-      }
-      const uint32_t row_s = base_s + kOffA + tid * 128;
-#pragma unroll
-      for (int c = 0; c < 8; ++c)
-        tc::sts128(row_s + ((c ^ (tid & 7)) << 4), wv[4 * c], wv[4 * c + 1], wv[4 * c + 2], wv[4 * c + 3]);
-      tc::fence_proxy_async();
-    }
-    // 4. one tensor-core round per genome present in the tile
+    const uint32_t row_s = a_s + tid * 128;
     bool done = g < 0;
     float act[kOut], zo[kOut];
 #pragma unroll
     for (int o = 0; o < kOut; ++o) act[o] = zo[o] = 0.0f;
+    // one tensor-core round per genome present in the tile (first pending row's genome)
     while (true) {
       const unsigned b = __ballot_sync(0xffffffffu, !done);
       if (lane == 0) ballots[warp] = b;
@@ -156,19 +156,51 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
       __syncthreads();
       const int gs = *sel;
       if (gs < 0) break;
-      if (*wgenome != gs) {                                      // stage this genome's BF16 blob
+      if (*wgenome != gs) {                           // stage this genome's BF16 blob
         const uint4* src = reinterpret_cast<const uint4*>(a.nets16 + (long long)gs * a.blob_bytes);
-        for (int i = tid; i < a.blob_bytes / 16; i += kThreads) {
-          const uint4 v = __ldg(src + i);
-          tc::sts128(w_s + i * 16, v.x, v.y, v.z, v.w);
+        const int n16 = a.blob_bytes >> 4;             // <= 648 = 6 x 108 per thread slot
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          uint4 v[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const int i = tid + (3 * half + k) * kThreads;
+            if (i < n16) v[k] = __ldg(src + i);
+          }
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const int i = tid + (3 * half + k) * kThreads;
+            if (i < n16) tc::sts128(w_s + i * 16, v[k].x, v[k].y, v[k].z, v[k].w);
+          }
         }
-        tc::fence_proxy_async();
-        __syncthreads();
-        if (tid == 0) *wgenome = gs;
       }
+      // this cell's input row: 9 records in kernel-rank order, 1.0 at K = 54, swizzled
+      {
+        uint32_t wv[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) wv[i] = 0u;
+        if (valid) {
+          uint4 rc = tc::lds128(rec_s + hc * 16);
+          wv[0] = rc.x; wv[1] = rc.y; wv[2] = rc.z;
+#pragma unroll
+          for (int p = 1; p < 9; ++p) {
+            int dx, dy;
+            octant_offset((2 * r + rank_delta(p)) & 7, dx, dy);
+            rc = tc::lds128(rec_s + (hc + dy * kHaloW + dx) * 16);
+            wv[3 * p] = rc.x; wv[3 * p + 1] = rc.y; wv[3 * p + 2] = rc.z;
+          }
+          wv[27] = 0x3F80u;                  // bf16 1.0 at K = 54 (layer-1 bias), 0 at K = 55
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          tc::sts128(row_s + ((c ^ (tid & 7)) << 4), wv[4 * c], wv[4 * c + 1], wv[4 * c + 2], wv[4 * c + 3]);
+      }
+      tc::fence_proxy_async();
+      __syncthreads();
       if (tid == 0) {
+        *wgenome = gs;
         tc::tc_fence_after();
-        const uint64_t ad = tc::sdesc_sw128(base_s + kOffA), bd = tc::sdesc_sw128(w_s);
+        const uint64_t ad = tc::sdesc_sw128(a_s), bd = tc::sdesc_sw128(w_s);
 #pragma unroll
         for (int k = 0; k < 4; ++k) tc::mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc1, k > 0);
         tc::mma_commit(mbar);
@@ -190,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
           }
         }
       } else {
-        const uint32_t row2 = base_s + kOffA2 + tid * 128;
+        // hidden layer: tanh, BF16, written over this row of the (consumed) input tile
         for (int c16 = 0; c16 < N1 / 16; ++c16) {
           float v[16];
           tc::tmem_ld16(t_lane + c16 * 16, v);
@@ -199,8 +231,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
             uint32_t pk[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) pk[i] = tc::pack_bf16x2(tc::tanh_approx(v[2 * i]), tc::tanh_approx(v[2 * i + 1]));
-            tc::sts128(row2 + (((2 * c16) ^ (tid & 7)) << 4), pk[0], pk[1], pk[2], pk[3]);
-            tc::sts128(row2 + (((2 * c16 + 1) ^ (tid & 7)) << 4), pk[4], pk[5], pk[6], pk[7]);
+            tc::sts128(row_s + (((2 * c16) ^ (tid & 7)) << 4), pk[0], pk[1], pk[2], pk[3]);
+            tc::sts128(row_s + (((2 * c16 + 1) ^ (tid & 7)) << 4), pk[4], pk[5], pk[6], pk[7]);
           }
         }
         tc::fence_proxy_async();
@@ -208,8 +240,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
         __syncthreads();
         if (tid == 0) {
           tc::tc_fence_after();
-          const uint64_t ad = tc::sdesc_sw128(base_s + kOffA2), bd = tc::sdesc_sw128(w_s + bf16_w2_off(H));
-          for (int k = 0; k < N1 / 16; ++k) tc::mma_bf16(tmem + kL2Col, ad + 2 * k, bd + 2 * k, idesc2, k > 0);
+          const uint64_t ad = tc::sdesc_sw128(a_s), bd = tc::sdesc_sw128(w_s + bf16_w2_off(H));
+          for (int k = 0; k < N1 / 16; ++k) tc::mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc2, k > 0);
           tc::mma_commit(mbar);
         }
         ok = tc::mbar_wait(mbar, phase, kWaitCycles);
@@ -217,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
         tc::tc_fence_after();
         float v[16];
-        tc::tmem_ld16(t_lane + kL2Col, v);
+        tc::tmem_ld16(t_lane, v);
         tc::tmem_wait_ld();
         if (mine) {
           const float* b2 = reinterpret_cast<const float*>(base + kOffW + bf16_b2_off(H));
@@ -232,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
       if (mine) done = true;
     }
     if (timed_out) break;
-    // 5. actuator epilogue and pass-1 stores
+    // actuator epilogue and pass-1 stores
     CellOut o;
     o.C[0] = o.C[1] = o.C[2] = o.C[3] = 0.0f;
     o.xdir = kNoExplore;
@@ -249,8 +281,8 @@ __global__ void __launch_bounds__(kThreads, 4) k_pass1_bf16(const StepArgs a) {
     }
     const int ex = warp_sum_i(valid && o.xdir != kNoExplore ? 1 : 0);
     if (lane == 0) accX += ex;
-    __syncthreads();   // stage / records / tiles are rewritten by the next tile
   }
+  tc::cp_async_wait_all();                            // no copy may land after the CTA exits
 
   if (timed_out && tid == 0) atomicCAS(a.status, 0, (int)CORAL_E_TIMEOUT);
   if (lane == 0) {
@@ -292,7 +324,7 @@ int pass1_bf16_grid(int sms) {
     cudaGetLastError();
     return 0;
   }
-  if (per_sm > 4) per_sm = 4;                                 // 4 x 128 TMEM columns per SM
+  if (per_sm > kCtasPerSm) per_sm = kCtasPerSm;               // kCtasPerSm x 64 TMEM columns <= 512
   if (per_sm < 1) return 0;
   const int g = per_sm * sms;
   return g > kMaxPartials ? kMaxPartials : g;

@@ -181,8 +181,9 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(const StepArgs a) {
       int32_t g = a.cur.G[j];
       uint8_t r = a.cur.R[j];
       if (take) {
-        g = a.cur.G[nb[bd]];
-        r = a.p1.xdir[nb[bd]];
+        const long long nw = bd == 0 ? nb[0] : (bd == 1 ? nb[1] : (bd == 2 ? nb[2] : nb[3]));
+        g = a.cur.G[nw];
+        r = a.p1.xdir[nw];
       }
       const float inflow = ((a.p1.q[nb[0]] + a.p1.q[nb[1]]) + a.p1.q[nb[2]]) + a.p1.q[nb[3]];
       const float E2 = a.p1.keep[j] + a.cur.I[j] * inflow;
