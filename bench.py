@@ -236,6 +236,7 @@ def run_coral(a, rank, world_size, local):
     pid = coral.BF16_GROUPED if path == "bf16" else coral.FP32_PERCELL
     N = w.n_cells
     sub = coral.substrate_for_world(w, pid, stream=stream)
+    launch = sub.launch_config()
 
     # warm-up, then K timed steps bracketed by barrier + synchronize
     sub.step(a.warmup)
@@ -330,7 +331,7 @@ def run_coral(a, rank, world_size, local):
                    "height": w.height, "genomes": w.n_genomes, "hidden": w.hidden,
                    "l2": "no flush: state 487 MB per buffer > 129 MB L2" if a.workload == "cfg3" else
                    "state smaller than L2",
-                   "parallelism": f"independent worlds x{world_size}"},
+                   "parallelism": f"independent worlds x{world_size}", "launch": launch},
         "p50_step_ms": float(np.percentile(step_ms, 50)), "p99_step_ms": float(np.percentile(step_ms, 99)),
         "stage_ms": {"pass1": p1_ms, "pass2": p2_ms, "rest": float(np.mean(stage_ms[:, 2]))},
         "roofline": roof,

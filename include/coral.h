@@ -201,6 +201,11 @@ int coral_read_weights(coral_substrate* s, int32_t slot, float* dst, size_t dst_
 int coral_set_step(coral_substrate* s, int64_t t);
 int coral_get_step(const coral_substrate* s, int64_t* t);
 
+/* Launch configuration chosen at creation (tracing): CTAs of pass 1 and pass 2 and the SM
+ * count of the device. Any pointer may be NULL. */
+int coral_launch_config(const coral_substrate* s, int32_t* grid_pass1, int32_t* grid_pass2,
+                        int32_t* sms);
+
 /* Waits for the stream and returns the first latched device-side error, if any. */
 int coral_sync(coral_substrate* s);
 

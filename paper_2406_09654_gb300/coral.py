@@ -75,6 +75,7 @@ SIGNATURES = {
     "coral_set_step": (ctypes.c_int, [_VP, _I64]),
     "coral_get_step": (ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
     "coral_sync": (ctypes.c_int, [_VP]),
+    "coral_launch_config": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "coral_last_error": (ctypes.c_char_p, [_VP]),
     "coral_net_floats": (_I32, [_I32]),
 }
@@ -239,6 +240,11 @@ class Substrate:
 
     def sync(self):
         _check(lib().coral_sync(self.h), self.h)
+
+    def launch_config(self):
+        v = (ctypes.c_int32 * 3)()
+        _check(lib().coral_launch_config(self.h, ctypes.byref(v, 0), ctypes.byref(v, 4), ctypes.byref(v, 8)), self.h)
+        return {"grid_pass1": v[0], "grid_pass2": v[1], "sms": v[2]}
 
     # -- reads
     def read_channels(self, mask=CH_ALL, out=None):

@@ -515,6 +515,14 @@ int coral_get_step(const coral_substrate* s, int64_t* t) {
   return CORAL_OK;
 }
 
+int coral_launch_config(const coral_substrate* s, int32_t* g1, int32_t* g2, int32_t* sms) {
+  if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
+  if (g1) *g1 = s->grid1;
+  if (g2) *g2 = s->grid2;
+  if (sms) *sms = s->sms;
+  return CORAL_OK;
+}
+
 int coral_sync(coral_substrate* s) {
   if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
   return check_status(s);

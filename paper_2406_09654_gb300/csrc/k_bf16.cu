@@ -310,12 +310,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
 size_t pass1_bf16_smem() { return kSmemBytes; }
 
 int pass1_bf16_grid(int sms) {
-  int dev = 0, major = 0, minor = 0;
+  int dev = 0, major = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
-  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
-  if (major != 10) return 0;                                  // tcgen05 needs sm_100 family
-  if (cudaFuncSetAttribute(k_pass1_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess) {
+  if (major != 10) return 0;                                  // tcgen05 needs the sm_100 family
+  if (cudaFuncSetAttribute(k_pass1_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
+      cudaFuncSetAttribute(k_pass1_bf16, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -324,7 +325,21 @@ int pass1_bf16_grid(int sms) {
     cudaGetLastError();
     return 0;
   }
-  if (per_sm > kCtasPerSm) per_sm = kCtasPerSm;               // kCtasPerSm x 64 TMEM columns <= 512
+  // Residency is bounded by TMEM (kCtasPerSm x 64 of 512 columns) and by the register and
+  // shared-memory budgets the kernel was compiled for, which allow kCtasPerSm.
+  if (per_sm < kCtasPerSm) {
+    int smem_sm = 0, regs_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_pass1_bf16) == cudaSuccess) {
+      const int by_smem = smem_sm / (kSmemBytes + (int)fa.sharedSizeBytes + 1024);
+      const int by_regs = regs_sm / (fa.numRegs * kThreads);
+      int est = by_smem < by_regs ? by_smem : by_regs;
+      if (est > per_sm) per_sm = est;
+    }
+  }
+  if (per_sm > kCtasPerSm) per_sm = kCtasPerSm;
   if (per_sm < 1) return 0;
   const int g = per_sm * sms;
   return g > kMaxPartials ? kMaxPartials : g;
