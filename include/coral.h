@@ -212,6 +212,26 @@ int coral_sync(coral_substrate* s);
 /* Message for the last error on s (or a generic one when s is NULL). Never NULL. */
 const char* coral_last_error(const coral_substrate* s);
 
+/*
+ * Allocation-free bucketing. The paper has no counterpart: this is a library convenience for
+ * callers that cannot allocate device memory when they need the sort — code running inside a
+ * stream capture they do not own, real-time loops where an allocator call may synchronise the
+ * device or fail under memory pressure, hosts that give the library a fixed memory budget.
+ * Same result as coral_read_perm (stable counting sort of cell ids by genome slot), on
+ * caller-owned device buffers: G [n_cells] int32 in [0, capacity), counts [capacity] int32 and
+ * perm [n_cells] int32 (outputs). Work is enqueued on cuda_stream (NULL = legacy default
+ * stream); the call returns after enqueueing and allocates nothing.
+ * Limits: n_cells <= 1,048,576 and capacity <= 65,536, else CORAL_E_INVALID with a message in
+ * coral_bucket_noalloc_last_error(). The scratch is one fixed 12.3 MiB device array per GPU
+ * that loads the library, kept until the process exits, shared by every call: calls that
+ * overlap on the GPU (different streams, no ordering) race on it and corrupt each other's
+ * results. The first call on each device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.
+ */
+int coral_bucket_noalloc(const int32_t* G, int64_t n_cells, int32_t capacity, int32_t* counts,
+                         int32_t* perm, void* cuda_stream);
+const char* coral_bucket_noalloc_last_error(void);
+
 /* Floats in one dense net for a given hidden size (the dense_or_null row length). */
 int32_t coral_net_floats(int32_t hidden);
 

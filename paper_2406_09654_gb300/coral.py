@@ -78,6 +78,8 @@ SIGNATURES = {
     "coral_launch_config": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "coral_last_error": (ctypes.c_char_p, [_VP]),
     "coral_net_floats": (_I32, [_I32]),
+    "coral_bucket_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _VP]),
+    "coral_bucket_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
 _lib = None
@@ -321,3 +323,20 @@ def bf16_available() -> bool:
         return True
     except CoralError:
         return False
+
+
+NOALLOC_MAX_CELLS = 1 << 20
+NOALLOC_MAX_CAPACITY = 1 << 16
+
+
+def bucket_noalloc(G, capacity, counts, perm, stream=None):
+    """Stable counting sort of cell ids by genome slot on caller-owned CUDA tensors, with no
+    device allocation (fixed library scratch; see coral_bucket_noalloc in include/coral.h).
+    G: int32 [n] (n <= 1,048,576), counts: int32 [capacity] (<= 65,536), perm: int32 [n]."""
+    sp = None
+    if stream is not None:
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    rc = lib().coral_bucket_noalloc(_ptr(G)[0], int(G.numel()), int(capacity), _ptr(counts)[0],
+                                    _ptr(perm)[0], sp)
+    if rc != OK:
+        raise CoralError(rc, lib().coral_bucket_noalloc_last_error().decode())
