@@ -38,22 +38,29 @@ constexpr int kOffG = kOffRec + kHaloCells * 16;          // int32 [128]
 constexpr int kOffMisc = kOffG + 512;                     // mbarrier, TMEM slot, flags
 constexpr int kSmemBytes = kOffMisc + 128 + 1024;         // + alignment slack
 
-__device__ __forceinline__ int modp(int v, int n) {
-  v %= n;
-  return v < 0 ? v + n : v;
+// v in [-1, n + tile) folded onto [0, n): one conditional step when the torus side is at least
+// the halo's (small), else a full modulo.
+__device__ __forceinline__ int fold(int v, int n, bool small) {
+  if (small) {
+    v %= n;
+    return v < 0 ? v + n : v;
+  }
+  return v < 0 ? v + n : (v >= n ? v - n : v);
 }
 
 // Starts the asynchronous copy of a tile's 34 x 6 halo of the six sensor planes (wrap-around)
 // into a stage buffer; one commit group per call.
-__device__ __forceinline__ void issue_halo(const StepArgs& a, long long tile, int tiles_x, uint32_t dst) {
-  const int x0 = (int)(tile % tiles_x) * kTileW, y0 = (int)(tile / tiles_x) * kTileH;
+__device__ __forceinline__ void issue_halo(const StepArgs& a, int tile, int tiles_x, uint32_t dst) {
+  const int ty = tile / tiles_x;
+  const int x0 = (tile - ty * tiles_x) * kTileW, y0 = ty * kTileH;
+  const bool small_w = a.W < kHaloW, small_h = a.H < kHaloH;
 #pragma unroll
   for (int k = 0; k < kLoadsPerThread; ++k) {
     const int i = threadIdx.x + k * kThreads;
     if (i < kStageFloats) {
       const int ch = i / kHaloCells, c = i - ch * kHaloCells;
       const int hy = c / kHaloW, hx = c - hy * kHaloW;
-      const long long n = (long long)modp(y0 - 1 + hy, a.H) * a.W + modp(x0 - 1 + hx, a.W);
+      const long long n = (long long)fold(y0 - 1 + hy, a.H, small_h) * a.W + fold(x0 - 1 + hx, a.W, small_w);
       const float* plane = ch == 0 ? a.cur.E : (ch == 1 ? a.cur.I : a.cur.C + (long long)(ch - 2) * a.N);
       tc::cp_async4(dst + 4 * i, plane + n);
     }
@@ -105,28 +112,48 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
   long long accX = 0;
   bool timed_out = false;
   const int tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (Hh + kTileH - 1) / kTileH;
-  const long long n_tiles = (long long)tiles_x * tiles_y;
+  const int n_tiles = tiles_x * tiles_y;
   // a contiguous run of tiles per CTA: neighbouring tiles share halo rows (L2) and genomes
-  const long long per = (n_tiles + gridDim.x - 1) / gridDim.x;
-  const long long t_begin = (long long)blockIdx.x * per;
-  const long long t_end = t_begin + per < n_tiles ? t_begin + per : n_tiles;
-  if (t_begin < t_end) issue_halo(a, t_begin, tiles_x, base_s + kOffStage);
+  const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
+  const int t_begin = blockIdx.x * per;
+  const int t_end = t_begin + per < n_tiles ? t_begin + per : n_tiles;
+  // this thread's cell of a tile, its genome and rotation (loaded one tile ahead)
+  auto cell_of = [&](int tile, int& gx, int& gy) {
+    const int ty = tile / tiles_x;
+    gx = (tile - ty * tiles_x) * kTileW + lane;
+    gy = ty * kTileH + warp;
+  };
+  int g_next = -1, r_next = 0;
+  auto load_gr = [&](int tile) {
+    int gx, gy;
+    cell_of(tile, gx, gy);
+    g_next = -1;
+    r_next = 0;
+    if (gx < W && gy < Hh) {
+      const int jn = gy * W + gx;
+      g_next = __ldg(a.cur.G + jn);
+      r_next = a.rotation ? (int)__ldg(a.cur.R + jn) : 0;
+    }
+  };
+  if (t_begin < t_end) {
+    issue_halo(a, t_begin, tiles_x, base_s + kOffStage);
+    load_gr(t_begin);
+  }
 
   int buf = 0;
-  for (long long tile = t_begin; tile < t_end; ++tile, buf ^= 1) {
-    const int x0 = (int)(tile % tiles_x) * kTileW, y0 = (int)(tile / tiles_x) * kTileH;
-    const int gx = x0 + lane, gy = y0 + warp;
+  for (int tile = t_begin; tile < t_end; ++tile, buf ^= 1) {
+    int gx, gy;
+    cell_of(tile, gx, gy);
     const bool valid = gx < W && gy < Hh;
     const long long j = (long long)gy * W + gx;
-    int g = -1, r = 0;
-    if (valid) {
-      g = __ldg(a.cur.G + j);
-      r = a.rotation ? (int)__ldg(a.cur.R + j) : 0;
-    }
+    const int g = g_next, r = r_next;
     tc::cp_async_wait_all();
     sG[tid] = g;
     __syncthreads();                                  // this tile's halo is in stage[buf]
-    if (tile + 1 < t_end) issue_halo(a, tile + 1, tiles_x, base_s + kOffStage + (buf ^ 1) * kStageBytes);
+    if (tile + 1 < t_end) {
+      issue_halo(a, tile + 1, tiles_x, base_s + kOffStage + (buf ^ 1) * kStageBytes);
+      load_gr(tile + 1);
+    }
     const float* stage = reinterpret_cast<const float*>(base + kOffStage + buf * kStageBytes);
     // BF16 records: the 6 channels of each halo cell in one 16-byte slot
     for (int c = tid; c < kHaloCells; c += kThreads) {

@@ -61,7 +61,8 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1_fp32(const StepArgs a) {
     o.C[0] = o.C[1] = o.C[2] = o.C[3] = 0.0f;
     o.xdir = kNoExplore;
     if (valid) {
-      const int x = (int)(j % W), y = (int)(j / W);
+      const int jj = (int)j;
+      const int y = jj / W, x = jj - y * W;
       const int r = a.rotation ? (int)a.cur.R[j] : 0;
       float in[kIn];
       load6(a.cur, j, N, in);
@@ -161,7 +162,8 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(const StepArgs a) {
     float E3 = 0.0f, I2 = 0.0f;
     bool take = false;
     if (valid) {
-      const int x = (int)(j % W), y = (int)(j / W);
+      const int jj = (int)j;
+      const int y = jj / W, x = jj - y * W;
       const long long yW = (long long)y * W;
       const long long nb[4] = {(long long)wrap(y - 1, H) * W + x, yW + wrap(x + 1, W),
                                (long long)wrap(y + 1, H) * W + x, yW + wrap(x - 1, W)};
@@ -196,6 +198,105 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(const StepArgs a) {
     warp_accumulate(E3, acc[0]);
     warp_accumulate(I2, acc[1]);
     const int tk = warp_sum_i(take ? 1 : 0);
+    if ((threadIdx.x & 31) == 0) accT[0] += tk;
+  }
+  block_partial<2, 1>(acc, accT, a.part2, 0, 1);
+}
+
+// Pass 2 for rows that are a multiple of 4 cells wide: each thread resolves 4 consecutive cells
+// of one row with 16-byte loads of the pass-1 buffers (same per-cell arithmetic and order as
+// k_pass2).
+__global__ void __launch_bounds__(kP2Threads) k_pass2_x4(const StepArgs a) {
+  const int W = a.W, H = a.H;
+  const int cpr = W >> 2;                       // chunks per row
+  const int n_chunks = cpr * H;
+  double acc[2] = {0, 0};
+  long long accT[1] = {0};
+  const int stride = gridDim.x * kP2Threads;
+  for (int base = blockIdx.x * kP2Threads; base < n_chunks; base += stride) {
+    const int c = base + threadIdx.x;
+    const bool valid = c < n_chunks;
+    float e_sum = 0.0f, i_sum = 0.0f;
+    int takes = 0;
+    if (valid) {
+      const int y = c / cpr;
+      const int x = (c - y * cpr) << 2;
+      const int j = y * W + x;
+      const int jn = (y == 0 ? H - 1 : y - 1) * W + x;          // same columns, row above
+      const int js = (y == H - 1 ? 0 : y + 1) * W + x;          // row below
+      const int jw = y * W + (x == 0 ? W - 1 : x - 1);          // left of the first cell
+      const int je = y * W + (x + 4 == W ? 0 : x + 4);          // right of the last cell
+      const float4 I1 = *reinterpret_cast<const float4*>(a.p1.I1 + j);
+      const float4 xa = *reinterpret_cast<const float4*>(a.p1.xamt + j);
+      const float4 kp = *reinterpret_cast<const float4*>(a.p1.keep + j);
+      const float4 It = *reinterpret_cast<const float4*>(a.cur.I + j);
+      const float4 qc = *reinterpret_cast<const float4*>(a.p1.q + j);
+      const float4 xaN = *reinterpret_cast<const float4*>(a.p1.xamt + jn);
+      const float4 xaS = *reinterpret_cast<const float4*>(a.p1.xamt + js);
+      const float4 qN = *reinterpret_cast<const float4*>(a.p1.q + jn);
+      const float4 qS = *reinterpret_cast<const float4*>(a.p1.q + js);
+      const uint32_t dc = *reinterpret_cast<const uint32_t*>(a.p1.xdir + j);
+      const uint32_t dN = *reinterpret_cast<const uint32_t*>(a.p1.xdir + jn);
+      const uint32_t dS = *reinterpret_cast<const uint32_t*>(a.p1.xdir + js);
+      const int4 Gc = *reinterpret_cast<const int4*>(a.cur.G + j);
+      const uint32_t Rc = *reinterpret_cast<const uint32_t*>(a.cur.R + j);
+      const uint8_t dW = a.p1.xdir[jw], dE = a.p1.xdir[je];
+      const float xaW = a.p1.xamt[jw], xaE = a.p1.xamt[je];
+      const float qW = a.p1.q[jw], qE = a.p1.q[je];
+      const float vI1[4] = {I1.x, I1.y, I1.z, I1.w}, vxa[4] = {xa.x, xa.y, xa.z, xa.w};
+      const float vkp[4] = {kp.x, kp.y, kp.z, kp.w}, vIt[4] = {It.x, It.y, It.z, It.w};
+      const float vq[4] = {qc.x, qc.y, qc.z, qc.w};
+      const float vxaN[4] = {xaN.x, xaN.y, xaN.z, xaN.w}, vxaS[4] = {xaS.x, xaS.y, xaS.z, xaS.w};
+      const float vqN[4] = {qN.x, qN.y, qN.z, qN.w}, vqS[4] = {qS.x, qS.y, qS.z, qS.w};
+      const int vG[4] = {Gc.x, Gc.y, Gc.z, Gc.w};
+      float oE[4], oI[4];
+      int oG[4];
+      uint32_t oR = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        // neighbours of cell x+k in N, E, S, W order: direction byte, amount, flow quotient
+        const uint32_t nd[4] = {(dN >> (8 * k)) & 0xFFu,
+                                k < 3 ? (dc >> (8 * (k + 1))) & 0xFFu : (uint32_t)dE,
+                                (dS >> (8 * k)) & 0xFFu,
+                                k > 0 ? (dc >> (8 * (k - 1))) & 0xFFu : (uint32_t)dW};
+        const float na[4] = {vxaN[k], k < 3 ? vxa[k + 1] : xaE, vxaS[k], k > 0 ? vxa[k - 1] : xaW};
+        const float nq[4] = {vqN[k], k < 3 ? vq[k + 1] : qE, vqS[k], k > 0 ? vq[k - 1] : qW};
+        float I2 = vI1[k] - vxa[k];
+        float best = -INFINITY;
+        int bd = -1;
+#pragma unroll
+        for (int D = 0; D < 4; ++D) {
+          if (nd[D] == (uint32_t)((D + 2) & 3)) {
+            I2 += na[D];
+            if (na[D] > best) { best = na[D]; bd = D; }
+          }
+        }
+        const bool take = bd >= 0 && best > vI1[k];
+        int g = vG[k];
+        uint32_t r = (Rc >> (8 * k)) & 0xFFu;
+        if (take) {
+          const int nb = bd == 0 ? jn + k : (bd == 2 ? js + k : (bd == 1 ? (k < 3 ? j + k + 1 : je) : (k > 0 ? j + k - 1 : jw)));
+          g = a.cur.G[nb];
+          r = bd == 0 ? nd[0] : (bd == 1 ? nd[1] : (bd == 2 ? nd[2] : nd[3]));
+          ++takes;
+        }
+        const float inflow = ((nq[0] + nq[1]) + nq[2]) + nq[3];
+        const float E2 = vkp[k] + vIt[k] * inflow;
+        oE[k] = a.is_day ? E2 + a.e_day : E2 - a.e_night * E2;
+        oI[k] = I2;
+        oG[k] = g;
+        oR |= r << (8 * k);
+        e_sum += oE[k];
+        i_sum += oI[k];
+      }
+      *reinterpret_cast<float4*>(a.nxt.E + j) = make_float4(oE[0], oE[1], oE[2], oE[3]);
+      *reinterpret_cast<float4*>(a.nxt.I + j) = make_float4(oI[0], oI[1], oI[2], oI[3]);
+      *reinterpret_cast<int4*>(a.nxt.G + j) = make_int4(oG[0], oG[1], oG[2], oG[3]);
+      *reinterpret_cast<uint32_t*>(a.nxt.R + j) = oR;
+    }
+    warp_accumulate(e_sum, acc[0]);
+    warp_accumulate(i_sum, acc[1]);
+    const int tk = warp_sum_i(takes);
     if ((threadIdx.x & 31) == 0) accT[0] += tk;
   }
   block_partial<2, 1>(acc, accT, a.part2, 0, 1);
@@ -255,7 +356,11 @@ int occupancy_grid(const void* fn, int threads, size_t smem, int sms) {
 }  // namespace
 
 int pass1_fp32_grid(int sms) { return occupancy_grid((const void*)k_pass1_fp32, kP1Threads, 0, sms); }
-int pass2_grid(int sms) { return occupancy_grid((const void*)k_pass2, kP2Threads, 0, sms); }
+int pass2_grid(int sms) {
+  const int a = occupancy_grid((const void*)k_pass2, kP2Threads, 0, sms);
+  const int b = occupancy_grid((const void*)k_pass2_x4, kP2Threads, 0, sms);
+  return a < b ? a : b;
+}
 
 cudaError_t launch_pass1_fp32(const StepArgs& a, cudaStream_t st, int grid) {
   k_pass1_fp32<<<grid, kP1Threads, 0, st>>>(a);
@@ -263,7 +368,10 @@ cudaError_t launch_pass1_fp32(const StepArgs& a, cudaStream_t st, int grid) {
 }
 
 cudaError_t launch_pass2(const StepArgs& a, cudaStream_t st, int grid) {
-  k_pass2<<<grid, kP2Threads, 0, st>>>(a);
+  if ((a.W & 3) == 0 && a.W >= 8)
+    k_pass2_x4<<<grid, kP2Threads, 0, st>>>(a);
+  else
+    k_pass2<<<grid, kP2Threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
