@@ -16,13 +16,22 @@ struct CellOut {
 // z[6..9]: pre-activations of the explore actuators (tanh is strictly increasing, so the
 // maximal actuator and its sign are read off z, where saturated outputs cannot tie).
 // E, I: the cell's state; S: FP64 sum of I_t over its 4 von Neumann neighbours; r: rotation.
+// kFast: hardware exp / reciprocal / reciprocal-square-root approximations (relative error
+// ~1e-6, far inside the BF16 path's tolerance); otherwise the accurate library functions.
+template <bool kFast = false>
 __device__ __forceinline__ void actuator_epilogue(const StepArgs& p, const float* a, const float* z,
                                                   float E, float I, double S, int r, CellOut& o) {
   // Communication: normalised by max(1, ||a0..3||) and passed through a sigmoid.
   const float n2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3];
-  const float nrm = fmaxf(1.0f, sqrtf(n2));
+  if (kFast) {
+    const float inv = n2 > 1.0f ? rsqrtf(n2) : 1.0f;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) o.C[k] = 1.0f / (1.0f + expf(-(a[k] / nrm)));
+    for (int k = 0; k < 4; ++k) o.C[k] = __fdividef(1.0f, 1.0f + __expf(-(a[k] * inv)));
+  } else {
+    const float nrm = fmaxf(1.0f, sqrtf(n2));
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o.C[k] = 1.0f / (1.0f + expf(-(a[k] / nrm)));
+  }
   // Invest moves inv*E into infrastructure, liquidate moves liq*I back into energy.
   const float inv = p.k_inv * fmaxf(a[4], 0.0f);
   const float liq = p.k_liq * fmaxf(a[5], 0.0f);
@@ -40,9 +49,10 @@ __device__ __forceinline__ void actuator_epilogue(const StepArgs& p, const float
   o.I1 = I1;
   // Energy flow along infrastructure: the cell keeps (1 - k_flow) E1 when it has somewhere
   // to send, and each neighbour j receives I_t(j) * q with q = k_flow E1 / S.
-  const bool send = S > 0.0;
+  const float Sf = (float)S;          // S >= 0 is a sum of floats: Sf > 0 exactly when S > 0
+  const bool send = Sf > 0.0f;
   o.keep = send ? E1 - p.k_flow * E1 : E1;
-  o.q = send ? (p.k_flow * E1) / (float)S : 0.0f;
+  o.q = send ? (kFast ? __fdividef(p.k_flow * E1, Sf) : (p.k_flow * E1) / Sf) : 0.0f;
 }
 
 __device__ __forceinline__ void store_pass1(const StepArgs& p, long long j, const CellOut& o) {

@@ -24,7 +24,6 @@ constexpr int kTileW = 32, kTileH = 4;
 constexpr int kHaloW = kTileW + 2, kHaloH = kTileH + 2;
 constexpr int kHaloCells = kHaloW * kHaloH;               // 204
 constexpr int kStageFloats = 6 * kHaloCells;              // 1224
-constexpr int kLoadsPerThread = (kStageFloats + kThreads - 1) / kThreads;
 constexpr uint32_t kTmemCols = 64;                        // layer 1, then layer 2 in cols 0..15
 constexpr long long kWaitCycles = 4000000000LL;           // about 2 s of SM clock
 
@@ -49,21 +48,19 @@ __device__ __forceinline__ int fold(int v, int n, bool small) {
 }
 
 // Starts the asynchronous copy of a tile's 34 x 6 halo of the six sensor planes (wrap-around)
-// into a stage buffer; one commit group per call.
-__device__ __forceinline__ void issue_halo(const StepArgs& a, int tile, int tiles_x, uint32_t dst) {
-  const int ty = tile / tiles_x;
-  const int x0 = (tile - ty * tiles_x) * kTileW, y0 = ty * kTileH;
-  const bool small_w = a.W < kHaloW, small_h = a.H < kHaloH;
-#pragma unroll
-  for (int k = 0; k < kLoadsPerThread; ++k) {
-    const int i = threadIdx.x + k * kThreads;
-    if (i < kStageFloats) {
-      const int ch = i / kHaloCells, c = i - ch * kHaloCells;
-      const int hy = c / kHaloW, hx = c - hy * kHaloW;
-      const long long n = (long long)fold(y0 - 1 + hy, a.H, small_h) * a.W + fold(x0 - 1 + hx, a.W, small_w);
-      const float* plane = ch == 0 ? a.cur.E : (ch == 1 ? a.cur.I : a.cur.C + (long long)(ch - 2) * a.N);
-      tc::cp_async4(dst + 4 * i, plane + n);
-    }
+// into a stage buffer [6][6][34] floats: warp w copies row segments w, w+4, ... (one per
+// channel and halo row); lane l copies column l, lanes 0 and 1 also columns 32 and 33.
+// col_a / col_b: the wrapped grid columns of this lane's halo column(s). One commit group.
+__device__ __forceinline__ void issue_halo(const StepArgs& a, int y0, int col_a, int col_b, uint32_t dst) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool small_h = a.H < kHaloH;
+  for (int sgm = warp; sgm < 6 * kHaloH; sgm += kThreads / 32) {
+    const int ch = sgm / kHaloH, hy = sgm - ch * kHaloH;
+    const float* plane = ch == 0 ? a.cur.E : (ch == 1 ? a.cur.I : a.cur.C + (long long)(ch - 2) * a.N);
+    const float* row = plane + (long long)fold(y0 - 1 + hy, a.H, small_h) * a.W;
+    const uint32_t d = dst + 4u * (uint32_t)(ch * kHaloCells + hy * kHaloW);
+    tc::cp_async4(d + 4u * lane, row + col_a);
+    if (lane < 2) tc::cp_async4(d + 4u * (32 + lane), row + col_b);
   }
   tc::cp_async_commit();
 }
@@ -77,7 +74,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
   uint64_t* mbar = reinterpret_cast<uint64_t*>(base + kOffMisc);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + kOffMisc + 8);
   int* wgenome = reinterpret_cast<int*>(base + kOffMisc + 12);
-  int* sel = reinterpret_cast<int*>(base + kOffMisc + 16);
   unsigned* ballots = reinterpret_cast<unsigned*>(base + kOffMisc + 20);
   __shared__ double red_s[4][4];
   __shared__ long long red_c[4];
@@ -124,9 +120,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
     gy = ty * kTileH + warp;
   };
   int g_next = -1, r_next = 0;
-  auto load_gr = [&](int tile) {
+  const bool small_w = W < kHaloW;
+  // next tile: halo copy started, genome and rotation of this thread's cell loaded
+  auto prefetch = [&](int tile, uint32_t dst) {
     int gx, gy;
     cell_of(tile, gx, gy);
+    const int x0 = gx - lane, y0 = gy - warp;
+    issue_halo(a, y0, fold(x0 - 1 + lane, W, small_w), fold(x0 + 31 + lane, W, small_w), dst);
     g_next = -1;
     r_next = 0;
     if (gx < W && gy < Hh) {
@@ -135,10 +135,9 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
       r_next = a.rotation ? (int)__ldg(a.cur.R + jn) : 0;
     }
   };
-  if (t_begin < t_end) {
-    issue_halo(a, t_begin, tiles_x, base_s + kOffStage);
-    load_gr(t_begin);
-  }
+  if (t_begin < t_end) prefetch(t_begin, base_s + kOffStage);
+  float cacc[4] = {0, 0, 0, 0};           // FP32 partials of up to 8 tiles, then into accC
+  int ntile = 0;
 
   int buf = 0;
   for (int tile = t_begin; tile < t_end; ++tile, buf ^= 1) {
@@ -150,10 +149,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
     tc::cp_async_wait_all();
     sG[tid] = g;
     __syncthreads();                                  // this tile's halo is in stage[buf]
-    if (tile + 1 < t_end) {
-      issue_halo(a, tile + 1, tiles_x, base_s + kOffStage + (buf ^ 1) * kStageBytes);
-      load_gr(tile + 1);
-    }
+    if (tile + 1 < t_end) prefetch(tile + 1, base_s + kOffStage + (buf ^ 1) * kStageBytes);
     const float* stage = reinterpret_cast<const float*>(base + kOffStage + buf * kStageBytes);
     // BF16 records: the 6 channels of each halo cell in one 16-byte slot
     for (int c = tid; c < kHaloCells; c += kThreads) {
@@ -174,14 +170,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
       const unsigned b = __ballot_sync(0xffffffffu, !done);
       if (lane == 0) ballots[warp] = b;
       __syncthreads();
-      if (tid == 0) {
-        int first = -1;
-        for (int w = 0; w < 4 && first < 0; ++w)
-          if (ballots[w]) first = w * 32 + __ffs(ballots[w]) - 1;
-        *sel = first < 0 ? -1 : sG[first];
+      int first = -1;
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const unsigned bw = ballots[w];
+        if (first < 0 && bw) first = w * 32 + __ffs(bw) - 1;
       }
-      __syncthreads();
-      const int gs = *sel;
+      const int gs = first < 0 ? -1 : sG[first];
       if (gs < 0) break;
       if (*wgenome != gs) {                           // stage this genome's BF16 blob
         const uint4* src = reinterpret_cast<const uint4*>(a.nets16 + (long long)gs * a.blob_bytes);
@@ -224,15 +219,16 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
       }
       tc::fence_proxy_async();
       __syncthreads();
-      if (tid == 0) {
+      bool ok = true;
+      if (tid == 0) {          // one thread issues and waits; the others park at the barrier
         *wgenome = gs;
         tc::tc_fence_after();
         const uint64_t ad = tc::sdesc_sw128(a_s), bd = tc::sdesc_sw128(w_s);
 #pragma unroll
         for (int k = 0; k < 4; ++k) tc::mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc1, k > 0);
         tc::mma_commit(mbar);
+        ok = tc::mbar_wait(mbar, phase, kWaitCycles);
       }
-      bool ok = tc::mbar_wait(mbar, phase, kWaitCycles);
       phase ^= 1;
       if (__syncthreads_or(!ok)) { timed_out = true; break; }
       tc::tc_fence_after();
@@ -270,8 +266,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
           const uint64_t ad = tc::sdesc_sw128(a_s), bd = tc::sdesc_sw128(w_s + bf16_w2_off(H));
           for (int k = 0; k < N1 / 16; ++k) tc::mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc2, k > 0);
           tc::mma_commit(mbar);
+          ok = tc::mbar_wait(mbar, phase, kWaitCycles);
         }
-        ok = tc::mbar_wait(mbar, phase, kWaitCycles);
         phase ^= 1;
         if (__syncthreads_or(!ok)) { timed_out = true; break; }
         tc::tc_fence_after();
@@ -298,20 +294,37 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
     if (valid) {
       const float* sI = stage + kHaloCells;
       const double S = (double)sI[hc - kHaloW] + (double)sI[hc + 1] + (double)sI[hc + kHaloW] + (double)sI[hc - 1];
-      actuator_epilogue(a, act, zo, stage[hc], sI[hc], S, r, o);
+      actuator_epilogue<true>(a, act, zo, stage[hc], sI[hc], S, r, o);
       store_pass1(a, j, o);
     }
+    if (valid) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const float s = warp_sum(valid ? o.C[k] : 0.0f);
-      if (lane == 0) accC[k] += (double)s;
+      for (int k = 0; k < 4; ++k) cacc[k] += o.C[k];
+      accX += o.xdir != kNoExplore ? 1 : 0;
     }
-    const int ex = warp_sum_i(valid && o.xdir != kNoExplore ? 1 : 0);
-    if (lane == 0) accX += ex;
+    if (++ntile == 8) {
+      ntile = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        accC[k] += (double)cacc[k];
+        cacc[k] = 0.0f;
+      }
+    }
   }
   tc::cp_async_wait_all();                            // no copy may land after the CTA exits
 
   if (timed_out && tid == 0) atomicCAS(a.status, 0, (int)CORAL_E_TIMEOUT);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    double v = accC[k] + (double)cacc[k];
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    accC[k] = v;
+  }
+  long long ex = accX;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) ex += __shfl_xor_sync(0xffffffffu, ex, off);
+  accX = ex;
   if (lane == 0) {
     for (int k = 0; k < 4; ++k) red_s[warp][k] = accC[k];
     red_c[warp] = accX;
