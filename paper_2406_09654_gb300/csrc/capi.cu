@@ -196,9 +196,12 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
     const long long N = s->N;
     bool ok = true;
     for (int b = 0; b < 2 && ok; ++b) {
-      ok &= dalloc(s, &s->st[b].E, N) == cudaSuccess;
-      ok &= dalloc(s, &s->st[b].I, N) == cudaSuccess;
-      ok &= dalloc(s, &s->st[b].C, 4 * N) == cudaSuccess;
+      // the six sensor planes are contiguous (E, I, C0..C3, N floats each): plane c = E + c * N
+      ok &= dalloc(s, &s->st[b].E, 6 * N) == cudaSuccess;
+      if (ok) {
+        s->st[b].I = s->st[b].E + N;
+        s->st[b].C = s->st[b].E + 2 * N;
+      }
       ok &= dalloc(s, &s->st[b].G, N) == cudaSuccess;
       ok &= dalloc(s, &s->st[b].R, N) == cudaSuccess;
     }

@@ -43,7 +43,7 @@ __host__ __device__ inline int bf16_blob_bytes(int H) {
   return (n + 127) & ~127;
 }
 
-struct Planes {
+struct Planes {     // the six sensor planes are contiguous: I = E + N, C = E + 2N
   float* E;
   float* I;
   float* C;        // 4 planes of N floats

@@ -23,7 +23,6 @@ constexpr int kCtasPerSm = 5;
 constexpr int kTileW = 32, kTileH = 4;
 constexpr int kHaloW = kTileW + 2, kHaloH = kTileH + 2;
 constexpr int kHaloCells = kHaloW * kHaloH;               // 204
-constexpr int kStageFloats = 6 * kHaloCells;              // 1224
 constexpr uint32_t kTmemCols = 64;                        // layer 1, then layer 2 in cols 0..15
 constexpr long long kWaitCycles = 4000000000LL;           // about 2 s of SM clock
 
@@ -47,17 +46,39 @@ __device__ __forceinline__ int fold(int v, int n, bool small) {
   return v < 0 ? v + n : (v >= n ? v - n : v);
 }
 
-// Starts the asynchronous copy of a tile's 34 x 6 halo of the six sensor planes (wrap-around)
-// into a stage buffer [6][6][34] floats: warp w copies row segments w, w+4, ... (one per
-// channel and halo row); lane l copies column l, lanes 0 and 1 also columns 32 and 33.
-// col_a / col_b: the wrapped grid columns of this lane's halo column(s). One commit group.
-__device__ __forceinline__ void issue_halo(const StepArgs& a, int y0, int col_a, int col_b, uint32_t dst) {
+// Record-index offset (dy * 34 + dx) of kernel ranks 1..8 for rotation r, one signed byte per
+// rank (rank p in bits 8(p-1)..8p-1), from the same octant tables as the FP32 path.
+__host__ __device__ constexpr unsigned long long rank_offsets(int r) {
+  unsigned long long v = 0;
+  for (int p = 1; p < 9; ++p) {
+    const int o = (2 * r + rank_delta(p)) & 7;
+    const int dx = (int)((0x1A9u >> (2 * o)) & 3u) - 1, dy = (int)((0x1A90u >> (2 * o)) & 3u) - 1;
+    v |= (unsigned long long)(uint8_t)(int8_t)(dy * kHaloW + dx) << (8 * (p - 1));
+  }
+  return v;
+}
+
+// Starts the asynchronous copy of a tile's 34 x 6 halo of the six contiguous sensor planes into
+// a stage buffer [6][6][34] floats: warp w copies row segments w, w+4, ... (one per channel
+// and halo row); lane l copies column l, lanes 0 and 1 also columns 32 and 33. seg_off[k]:
+// channel * N + halo-row * W of this warp's k-th segment (interior tiles); col_a / col_b: the
+// wrapped grid columns of this lane's halo column(s). One commit group.
+__device__ __forceinline__ void issue_halo(const StepArgs& a, int y0, int col_a, int col_b, uint32_t dst,
+                                           const long long* seg_off) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool wraps = y0 == 0 || y0 - 1 + kHaloH > a.H;
+  const long long row0 = (long long)(y0 - 1) * a.W;
   const bool small_h = a.H < kHaloH;
-  for (int sgm = warp; sgm < 6 * kHaloH; sgm += kThreads / 32) {
+#pragma unroll
+  for (int k = 0; k < 6 * kHaloH / (kThreads / 32); ++k) {
+    const int sgm = warp + k * (kThreads / 32);
     const int ch = sgm / kHaloH, hy = sgm - ch * kHaloH;
-    const float* plane = ch == 0 ? a.cur.E : (ch == 1 ? a.cur.I : a.cur.C + (long long)(ch - 2) * a.N);
-    const float* row = plane + (long long)fold(y0 - 1 + hy, a.H, small_h) * a.W;
+    long long off;
+    if (!wraps)
+      off = seg_off[k] + row0;
+    else
+      off = (long long)ch * a.N + (long long)fold(y0 - 1 + hy, a.H, small_h) * a.W;
+    const float* row = a.cur.E + off;
     const uint32_t d = dst + 4u * (uint32_t)(ch * kHaloCells + hy * kHaloW);
     tc::cp_async4(d + 4u * lane, row + col_a);
     if (lane < 2) tc::cp_async4(d + 4u * (32 + lane), row + col_b);
@@ -121,12 +142,19 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
   };
   int g_next = -1, r_next = 0;
   const bool small_w = W < kHaloW;
+  long long seg_off[6 * kHaloH / (kThreads / 32)];   // this warp's segments: ch * N + hy * W
+#pragma unroll
+  for (int k = 0; k < 6 * kHaloH / (kThreads / 32); ++k) {
+    const int sgm = warp + k * (kThreads / 32);
+    const int ch = sgm / kHaloH, hy = sgm - ch * kHaloH;
+    seg_off[k] = (long long)ch * a.N + (long long)hy * W;
+  }
   // next tile: halo copy started, genome and rotation of this thread's cell loaded
   auto prefetch = [&](int tile, uint32_t dst) {
     int gx, gy;
     cell_of(tile, gx, gy);
     const int x0 = gx - lane, y0 = gy - warp;
-    issue_halo(a, y0, fold(x0 - 1 + lane, W, small_w), fold(x0 + 31 + lane, W, small_w), dst);
+    issue_halo(a, y0, fold(x0 - 1 + lane, W, small_w), fold(x0 + 31 + lane, W, small_w), dst, seg_off);
     g_next = -1;
     r_next = 0;
     if (gx < W && gy < Hh) {
@@ -202,13 +230,15 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
 #pragma unroll
         for (int i = 0; i < 32; ++i) wv[i] = 0u;
         if (valid) {
-          uint4 rc = tc::lds128(rec_s + hc * 16);
+          const uint32_t c_s = rec_s + hc * 16;
+          uint4 rc = tc::lds128(c_s);
           wv[0] = rc.x; wv[1] = rc.y; wv[2] = rc.z;
+          const unsigned long long offs = r == 0 ? rank_offsets(0) : r == 1 ? rank_offsets(1)
+                                        : r == 2 ? rank_offsets(2) : rank_offsets(3);
 #pragma unroll
           for (int p = 1; p < 9; ++p) {
-            int dx, dy;
-            octant_offset((2 * r + rank_delta(p)) & 7, dx, dy);
-            rc = tc::lds128(rec_s + (hc + dy * kHaloW + dx) * 16);
+            const int off = (int)(int8_t)(uint8_t)(offs >> (8 * (p - 1)));
+            rc = tc::lds128(c_s + off * 16);
             wv[3 * p] = rc.x; wv[3 * p + 1] = rc.y; wv[3 * p + 2] = rc.z;
           }
           wv[27] = 0x3F80u;                  // bf16 1.0 at K = 54 (layer-1 bias), 0 at K = 55
