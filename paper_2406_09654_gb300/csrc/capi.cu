@@ -205,9 +205,7 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
       ok &= dalloc(s, &s->st[b].G, N) == cudaSuccess;
       ok &= dalloc(s, &s->st[b].R, N) == cudaSuccess;
     }
-    ok = ok && dalloc(s, &s->p1.keep, N) == cudaSuccess && dalloc(s, &s->p1.q, N) == cudaSuccess &&
-         dalloc(s, &s->p1.I1, N) == cudaSuccess && dalloc(s, &s->p1.xamt, N) == cudaSuccess &&
-         dalloc(s, &s->p1.xdir, N) == cudaSuccess;
+    ok = ok && dalloc(s, &s->p1.rec, N) == cudaSuccess && dalloc(s, &s->p1.xdir, N) == cudaSuccess;
     s->g.hidden = p->hidden;
     s->g.capacity = genome_capacity;
     s->g.net_stride = net32_stride(p->hidden);

@@ -51,11 +51,13 @@ struct Planes {     // the six sensor planes are contiguous: I = E + N, C = E + 
   uint8_t* R;
 };
 
+// Pass-1 record of one cell, 16 bytes (one vector store / load):
+//   x = keep: E1 minus what the cell sends along infrastructure
+//   y = I1:   infrastructure after invest / liquidate
+//   z = q:    k_flow * E1 / S (FP64 denominator), what each neighbour gets per unit of I_t
+//   w = xamt: exploration amount (0 when not exploring)
 struct Pass1Bufs {
-  float* keep;     // E1 minus what the cell sends along infrastructure
-  float* q;        // k_flow * E1 / S (FP64 denominator), what each neighbour gets per unit I_t
-  float* I1;       // infrastructure after invest / liquidate
-  float* xamt;     // exploration amount (0 when not exploring)
+  float4* rec;     // [N]
   uint8_t* xdir;   // exploration direction 0..3 (N,E,S,W) or kNoExplore
 };
 

@@ -193,7 +193,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
     float act[kOut], zo[kOut];
 #pragma unroll
     for (int o = 0; o < kOut; ++o) act[o] = zo[o] = 0.0f;
-    // one tensor-core round per genome present in the tile (first pending row's genome)
+    // one tensor-core round per genome present in the tile (first pending row's genome); the
+    // input rows of pending cells survive a round (only finished rows are overwritten by their
+    // hidden values), so the input tile is built once per tile
+    bool first_round = true;
     while (true) {
       const unsigned b = __ballot_sync(0xffffffffu, !done);
       if (lane == 0) ballots[warp] = b;
@@ -225,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
         }
       }
       // this cell's input row: 9 records in kernel-rank order, 1.0 at K = 54, swizzled
-      {
+      if (first_round) {
         uint32_t wv[32];
 #pragma unroll
         for (int i = 0; i < 32; ++i) wv[i] = 0u;
@@ -315,6 +318,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
       }
       tc::tc_fence_before();
       if (mine) done = true;
+      first_round = false;
     }
     if (timed_out) break;
     // actuator epilogue and pass-1 stores

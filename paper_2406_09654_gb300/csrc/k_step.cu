@@ -167,14 +167,18 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(const StepArgs a) {
       const long long yW = (long long)y * W;
       const long long nb[4] = {(long long)wrap(y - 1, H) * W + x, yW + wrap(x + 1, W),
                                (long long)wrap(y + 1, H) * W + x, yW + wrap(x - 1, W)};
-      const float I1 = a.p1.I1[j];
-      I2 = I1 - a.p1.xamt[j];
+      const float4 me = a.p1.rec[j];                        // keep, I1, q, xamt
+      const float I1 = me.y;
+      I2 = I1 - me.w;
       float best = -INFINITY;
       int bd = -1;
+      float qn[4];
 #pragma unroll
       for (int D = 0; D < 4; ++D) {
+        const float2 nqx = *reinterpret_cast<const float2*>(&a.p1.rec[nb[D]].z);   // q, xamt
+        qn[D] = nqx.x;
         if (a.p1.xdir[nb[D]] == (uint8_t)((D + 2) & 3)) {   // neighbour explores toward j
-          const float xi = a.p1.xamt[nb[D]];
+          const float xi = nqx.y;
           I2 += xi;
           if (xi > best) { best = xi; bd = D; }             // strict: N, E, S, W keep ties
         }
@@ -187,8 +191,8 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(const StepArgs a) {
         g = a.cur.G[nw];
         r = a.p1.xdir[nw];
       }
-      const float inflow = ((a.p1.q[nb[0]] + a.p1.q[nb[1]]) + a.p1.q[nb[2]]) + a.p1.q[nb[3]];
-      const float E2 = a.p1.keep[j] + a.cur.I[j] * inflow;
+      const float inflow = ((qn[0] + qn[1]) + qn[2]) + qn[3];
+      const float E2 = me.x + a.cur.I[j] * inflow;
       E3 = a.is_day ? E2 + a.e_day : E2 - a.e_night * E2;
       a.nxt.E[j] = E3;
       a.nxt.I[j] = I2;
@@ -226,28 +230,30 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2_x4(const StepArgs a) {
       const int js = (y == H - 1 ? 0 : y + 1) * W + x;          // row below
       const int jw = y * W + (x == 0 ? W - 1 : x - 1);          // left of the first cell
       const int je = y * W + (x + 4 == W ? 0 : x + 4);          // right of the last cell
-      const float4 I1 = *reinterpret_cast<const float4*>(a.p1.I1 + j);
-      const float4 xa = *reinterpret_cast<const float4*>(a.p1.xamt + j);
-      const float4 kp = *reinterpret_cast<const float4*>(a.p1.keep + j);
+      float4 rc[4], rn[4], rs[4];                               // keep, I1, q, xamt
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        rc[k] = a.p1.rec[j + k];
+        rn[k] = a.p1.rec[jn + k];
+        rs[k] = a.p1.rec[js + k];
+      }
       const float4 It = *reinterpret_cast<const float4*>(a.cur.I + j);
-      const float4 qc = *reinterpret_cast<const float4*>(a.p1.q + j);
-      const float4 xaN = *reinterpret_cast<const float4*>(a.p1.xamt + jn);
-      const float4 xaS = *reinterpret_cast<const float4*>(a.p1.xamt + js);
-      const float4 qN = *reinterpret_cast<const float4*>(a.p1.q + jn);
-      const float4 qS = *reinterpret_cast<const float4*>(a.p1.q + js);
       const uint32_t dc = *reinterpret_cast<const uint32_t*>(a.p1.xdir + j);
       const uint32_t dN = *reinterpret_cast<const uint32_t*>(a.p1.xdir + jn);
       const uint32_t dS = *reinterpret_cast<const uint32_t*>(a.p1.xdir + js);
       const int4 Gc = *reinterpret_cast<const int4*>(a.cur.G + j);
       const uint32_t Rc = *reinterpret_cast<const uint32_t*>(a.cur.R + j);
       const uint8_t dW = a.p1.xdir[jw], dE = a.p1.xdir[je];
-      const float xaW = a.p1.xamt[jw], xaE = a.p1.xamt[je];
-      const float qW = a.p1.q[jw], qE = a.p1.q[je];
-      const float vI1[4] = {I1.x, I1.y, I1.z, I1.w}, vxa[4] = {xa.x, xa.y, xa.z, xa.w};
-      const float vkp[4] = {kp.x, kp.y, kp.z, kp.w}, vIt[4] = {It.x, It.y, It.z, It.w};
-      const float vq[4] = {qc.x, qc.y, qc.z, qc.w};
-      const float vxaN[4] = {xaN.x, xaN.y, xaN.z, xaN.w}, vxaS[4] = {xaS.x, xaS.y, xaS.z, xaS.w};
-      const float vqN[4] = {qN.x, qN.y, qN.z, qN.w}, vqS[4] = {qS.x, qS.y, qS.z, qS.w};
+      const float2 wq = *reinterpret_cast<const float2*>(&a.p1.rec[jw].z);
+      const float2 eq = *reinterpret_cast<const float2*>(&a.p1.rec[je].z);
+      const float xaW = wq.y, xaE = eq.y, qW = wq.x, qE = eq.x;
+      float vI1[4], vxa[4], vkp[4], vq[4], vxaN[4], vxaS[4], vqN[4], vqS[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        vkp[k] = rc[k].x; vI1[k] = rc[k].y; vq[k] = rc[k].z; vxa[k] = rc[k].w;
+        vqN[k] = rn[k].z; vxaN[k] = rn[k].w; vqS[k] = rs[k].z; vxaS[k] = rs[k].w;
+      }
+      const float vIt[4] = {It.x, It.y, It.z, It.w};
       const int vG[4] = {Gc.x, Gc.y, Gc.z, Gc.w};
       float oE[4], oI[4];
       int oG[4];
