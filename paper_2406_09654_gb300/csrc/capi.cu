@@ -22,6 +22,8 @@ struct coral_substrate {
   std::vector<void*> allocs;
   Planes st[2] = {};
   int cur = 0;
+  CUtensorMap tmap[2];          // TMA descriptors of the two state buffers' sensor planes
+  bool tmap_ok = false;
   Pass1Bufs p1 = {};
   GenomeArgs g = {};
   bool genomes_loaded = false;
@@ -237,6 +239,9 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
       break;
     }
     s->grid1 = p->path == CORAL_NET_BF16_GROUPED ? pass1_bf16_grid(s->sms) : pass1_fp32_grid(s->sms);
+    if (p->path == CORAL_NET_BF16_GROUPED)
+      s->tmap_ok = encode_sensor_tmap(&s->tmap[0], s->st[0].E, width, height) &&
+                   encode_sensor_tmap(&s->tmap[1], s->st[1].E, width, height);
     s->grid2 = pass2_grid(s->sms);
     if (s->grid1 < 1) {
       rc = fail(s, CORAL_E_CUDA, "the BF16 tensor-core kernel cannot be launched on this device");
@@ -336,7 +341,7 @@ int enqueue_step(coral_substrate* s, cudaEvent_t* ev) {
   StepArgs a = step_args(s);
   if (ev) CK(s, cudaEventRecord(ev[0], s->stream));
   if (s->p.path == CORAL_NET_BF16_GROUPED)
-    CK(s, launch_pass1_bf16(a, s->stream, s->grid1));
+    CK(s, launch_pass1_bf16(a, s->tmap_ok ? &s->tmap[s->cur] : nullptr, s->stream, s->grid1));
   else
     CK(s, launch_pass1_fp32(a, s->stream, s->grid1));
   if (ev) CK(s, cudaEventRecord(ev[1], s->stream));

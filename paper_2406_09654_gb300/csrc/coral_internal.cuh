@@ -1,6 +1,7 @@
 // Internal declarations of the GB300 substrate-step library (not part of the C ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -153,7 +154,11 @@ __device__ inline int warp_sum_i(int v) {
 
 // ---- launchers (defined in the .cu files) -----------------------------------------------
 cudaError_t launch_pass1_fp32(const StepArgs& a, cudaStream_t st, int grid);
-cudaError_t launch_pass1_bf16(const StepArgs& a, cudaStream_t st, int grid);
+// tmap: TMA descriptor of the current state's six sensor planes as a W x H x 6 float tensor
+// (box 40 x 6 x 6), or NULL when the grid does not allow it (then cp.async copies the halos).
+cudaError_t launch_pass1_bf16(const StepArgs& a, const CUtensorMap* tmap, cudaStream_t st, int grid);
+// Encodes that descriptor for planes starting at E (returns false when TMA cannot be used).
+bool encode_sensor_tmap(CUtensorMap* map, const float* E, int W, int H);
 cudaError_t launch_pass2(const StepArgs& a, cudaStream_t st, int grid);
 cudaError_t launch_stats(const StepArgs& a, int n_part1, int n_part2, long long t,
                          coral_stats* ring, cudaStream_t st);

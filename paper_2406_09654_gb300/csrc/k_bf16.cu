@@ -8,7 +8,9 @@
 // TMEM columns), one 128 x 16 x H MMA for layer 2. A tile with several genomes runs one round per
 // genome (the rows of other genomes are computed and discarded). The actuator
 // epilogue (communication, invest/liquidate, exploration, flow quotient) follows in registers.
+#include <cudaTypedefs.h>
 #include <math.h>
+#include <string.h>
 
 #include "coral_internal.cuh"
 #include "epilogue.cuh"
@@ -29,7 +31,10 @@ constexpr long long kWaitCycles = 4000000000LL;           // about 2 s of SM clo
 // shared memory layout, offsets from a 1024-byte aligned base
 constexpr int kOffA = 0;                                  // 128 x 128 B: input tile, then hidden tile
 constexpr int kOffW = 16384;                              // genome blob (<= 10368 B)
-constexpr int kStageBytes = 4928;                         // float32 [6][204], two buffers
+// stage: float32 [6 channels][6 rows][40 columns], halo column hx at 3 + hx (the TMA box starts
+// 4 cells left of the tile so its x coordinate stays 16-byte aligned), two buffers
+constexpr int kStageW = 40, kStageCh = kStageW * kHaloH;  // 240 floats per channel
+constexpr int kStageBytes = 6 * kStageCh * 4;             // 5760
 constexpr int kOffStage = kOffW + 11264;
 constexpr int kOffRec = kOffStage + 2 * kStageBytes;      // 204 x 16 B BF16 cell records
 constexpr int kOffG = kOffRec + kHaloCells * 16;          // int32 [128]
@@ -58,11 +63,11 @@ __host__ __device__ constexpr unsigned long long rank_offsets(int r) {
   return v;
 }
 
-// Starts the asynchronous copy of a tile's 34 x 6 halo of the six contiguous sensor planes into
-// a stage buffer [6][6][34] floats: warp w copies row segments w, w+4, ... (one per channel
-// and halo row); lane l copies column l, lanes 0 and 1 also columns 32 and 33. seg_off[k]:
-// channel * N + halo-row * W of this warp's k-th segment (interior tiles); col_a / col_b: the
-// wrapped grid columns of this lane's halo column(s). One commit group.
+// Starts the asynchronous copy (cp.async, for tiles whose halo wraps around the torus) of a
+// tile's 34 x 6 halo of the six contiguous sensor planes into a stage buffer: warp w copies row
+// segments w, w+4, ... (one per channel and halo row); lane l copies column l, lanes 0 and 1
+// also columns 32 and 33. seg_off[k]: channel * N + halo-row * W of this warp's k-th segment
+// (no vertical wrap); col_a / col_b: the wrapped grid columns of this lane's halo column(s).
 __device__ __forceinline__ void issue_halo(const StepArgs& a, int y0, int col_a, int col_b, uint32_t dst,
                                            const long long* seg_off) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -79,14 +84,15 @@ __device__ __forceinline__ void issue_halo(const StepArgs& a, int y0, int col_a,
     else
       off = (long long)ch * a.N + (long long)fold(y0 - 1 + hy, a.H, small_h) * a.W;
     const float* row = a.cur.E + off;
-    const uint32_t d = dst + 4u * (uint32_t)(ch * kHaloCells + hy * kHaloW);
+    const uint32_t d = dst + 4u * (uint32_t)(ch * kStageCh + hy * kStageW + 3);
     tc::cp_async4(d + 4u * lane, row + col_a);
     if (lane < 2) tc::cp_async4(d + 4u * (32 + lane), row + col_b);
   }
   tc::cp_async_commit();
 }
 
-__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepArgs a) {
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
+    k_pass1_bf16(const StepArgs a, const __grid_constant__ CUtensorMap tmap, const int use_tma) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_s = tc::smem_u32(smem_raw);
   const uint32_t base_s = (raw_s + 1023u) & ~1023u;
@@ -96,6 +102,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + kOffMisc + 8);
   int* wgenome = reinterpret_cast<int*>(base + kOffMisc + 12);
   unsigned* ballots = reinterpret_cast<unsigned*>(base + kOffMisc + 20);
+  uint64_t* halo_bar = reinterpret_cast<uint64_t*>(base + kOffMisc + 40);     // [2], one per stage
   __shared__ double red_s[4][4];
   __shared__ long long red_c[4];
 
@@ -113,6 +120,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
   }
   if (tid == 0) {
     tc::mbar_init(mbar, 1);
+    tc::mbar_init(&halo_bar[0], 1);
+    tc::mbar_init(&halo_bar[1], 1);
     tc::fence_barrier_init();
     *wgenome = -1;
   }
@@ -134,12 +143,6 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
   const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
   const int t_begin = blockIdx.x * per;
   const int t_end = t_begin + per < n_tiles ? t_begin + per : n_tiles;
-  // this thread's cell of a tile, its genome and rotation (loaded one tile ahead)
-  auto cell_of = [&](int tile, int& gx, int& gy) {
-    const int ty = tile / tiles_x;
-    gx = (tile - ty * tiles_x) * kTileW + lane;
-    gy = ty * kTileH + warp;
-  };
   int g_next = -1, r_next = 0;
   const bool small_w = W < kHaloW;
   long long seg_off[6 * kHaloH / (kThreads / 32)];   // this warp's segments: ch * N + hy * W
@@ -149,42 +152,73 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
     const int ch = sgm / kHaloH, hy = sgm - ch * kHaloH;
     seg_off[k] = (long long)ch * a.N + (long long)hy * W;
   }
+  uint32_t halo_phase = 0;                            // bit b: parity of halo_bar[b]
+  int tma_pending = -1;                               // stage buffer with a TMA copy in flight
+  // A tile's halo comes by one TMA box copy when it does not wrap around the torus, else by
+  // cp.async; the choice is uniform per tile.
+  auto tma_tile = [&](int x0, int y0) {
+    return use_tma && x0 >= 4 && x0 + kTileW + 4 <= W && y0 >= 1 && y0 + kTileH + 1 <= Hh;
+  };
   // next tile: halo copy started, genome and rotation of this thread's cell loaded
-  auto prefetch = [&](int tile, uint32_t dst) {
-    int gx, gy;
-    cell_of(tile, gx, gy);
-    const int x0 = gx - lane, y0 = gy - warp;
-    issue_halo(a, y0, fold(x0 - 1 + lane, W, small_w), fold(x0 + 31 + lane, W, small_w), dst, seg_off);
+  auto prefetch = [&](int x0, int y0, int b) {
+    const uint32_t dst = base_s + kOffStage + b * kStageBytes;
+    if (tma_tile(x0, y0)) {
+      if (tid == 0) {
+        tc::fence_proxy_async();                       // earlier generic accesses of the buffer
+        tc::mbar_expect_tx(&halo_bar[b], kStageBytes);
+        tc::tma_load_3d(dst, &tmap, x0 - 4, y0 - 1, 0, &halo_bar[b]);
+      }
+      tma_pending = b;
+    } else {
+      issue_halo(a, y0, fold(x0 - 1 + lane, W, small_w), fold(x0 + 31 + lane, W, small_w), dst, seg_off);
+    }
     g_next = -1;
     r_next = 0;
+    const int gx = x0 + lane, gy = y0 + warp;
     if (gx < W && gy < Hh) {
       const int jn = gy * W + gx;
       g_next = __ldg(a.cur.G + jn);
       r_next = a.rotation ? (int)__ldg(a.cur.R + jn) : 0;
     }
   };
-  if (t_begin < t_end) prefetch(t_begin, base_s + kOffStage);
+  int tx = t_begin % tiles_x, ty = t_begin / tiles_x;   // running tile coordinates
+  if (t_begin < t_end) prefetch(tx * kTileW, ty * kTileH, 0);
   float cacc[4] = {0, 0, 0, 0};           // FP32 partials of up to 8 tiles, then into accC
   int ntile = 0;
 
   int buf = 0;
   for (int tile = t_begin; tile < t_end; ++tile, buf ^= 1) {
-    int gx, gy;
-    cell_of(tile, gx, gy);
+    const int x0 = tx * kTileW, y0 = ty * kTileH;
+    if (++tx == tiles_x) {
+      tx = 0;
+      ++ty;
+    }
+    const int gx = x0 + lane, gy = y0 + warp;
     const bool valid = gx < W && gy < Hh;
     const long long j = (long long)gy * W + gx;
     const int g = g_next, r = r_next;
-    tc::cp_async_wait_all();
+    bool hok = true;
+    if (tma_tile(x0, y0)) {
+      if (tid == 0) hok = tc::mbar_wait(&halo_bar[buf], (halo_phase >> buf) & 1u, kWaitCycles);
+      halo_phase ^= 1u << buf;
+      tma_pending = -1;
+    } else {
+      tc::cp_async_wait_all();
+    }
     sG[tid] = g;
-    __syncthreads();                                  // this tile's halo is in stage[buf]
-    if (tile + 1 < t_end) prefetch(tile + 1, base_s + kOffStage + (buf ^ 1) * kStageBytes);
+    if (__syncthreads_or(!hok)) {                     // this tile's halo is in stage[buf]
+      timed_out = true;
+      break;
+    }
+    if (tile + 1 < t_end) prefetch(tx * kTileW, ty * kTileH, buf ^ 1);
     const float* stage = reinterpret_cast<const float*>(base + kOffStage + buf * kStageBytes);
     // BF16 records: the 6 channels of each halo cell in one 16-byte slot
     for (int c = tid; c < kHaloCells; c += kThreads) {
-      const float* s = stage + c;
-      tc::sts128(rec_s + c * 16, tc::pack_bf16x2(s[0], s[kHaloCells]),
-                 tc::pack_bf16x2(s[2 * kHaloCells], s[3 * kHaloCells]),
-                 tc::pack_bf16x2(s[4 * kHaloCells], s[5 * kHaloCells]), 0u);
+      const int hy = c / kHaloW;
+      const float* s = stage + hy * kStageW + (c - hy * kHaloW) + 3;
+      tc::sts128(rec_s + c * 16, tc::pack_bf16x2(s[0], s[kStageCh]),
+                 tc::pack_bf16x2(s[2 * kStageCh], s[3 * kStageCh]),
+                 tc::pack_bf16x2(s[4 * kStageCh], s[5 * kStageCh]), 0u);
     }
     __syncthreads();
     const int hc = (warp + 1) * kHaloW + (lane + 1);
@@ -326,9 +360,10 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
     o.C[0] = o.C[1] = o.C[2] = o.C[3] = 0.0f;
     o.xdir = kNoExplore;
     if (valid) {
-      const float* sI = stage + kHaloCells;
-      const double S = (double)sI[hc - kHaloW] + (double)sI[hc + 1] + (double)sI[hc + kHaloW] + (double)sI[hc - 1];
-      actuator_epilogue<true>(a, act, zo, stage[hc], sI[hc], S, r, o);
+      const int sc = (warp + 1) * kStageW + lane + 4;  // this cell in the stage layout
+      const float* sI = stage + kStageCh;
+      const double S = (double)sI[sc - kStageW] + (double)sI[sc + 1] + (double)sI[sc + kStageW] + (double)sI[sc - 1];
+      actuator_epilogue<true>(a, act, zo, stage[sc], sI[sc], S, r, o);
       store_pass1(a, j, o);
     }
     if (valid) {
@@ -346,6 +381,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16(const StepA
     }
   }
   tc::cp_async_wait_all();                            // no copy may land after the CTA exits
+  if (tid == 0 && tma_pending >= 0)
+    tc::mbar_wait(&halo_bar[tma_pending], (halo_phase >> tma_pending) & 1u, kWaitCycles);
 
   if (timed_out && tid == 0) atomicCAS(a.status, 0, (int)CORAL_E_TIMEOUT);
 #pragma unroll
@@ -419,9 +456,38 @@ int pass1_bf16_grid(int sms) {
   return g > kMaxPartials ? kMaxPartials : g;
 }
 
-cudaError_t launch_pass1_bf16(const StepArgs& a, cudaStream_t st, int grid) {
-  k_pass1_bf16<<<grid, kThreads, kSmemBytes, st>>>(a);
+cudaError_t launch_pass1_bf16(const StepArgs& a, const CUtensorMap* tmap, cudaStream_t st, int grid) {
+  CUtensorMap m;
+  if (tmap)
+    m = *tmap;
+  else
+    memset(&m, 0, sizeof(m));
+  k_pass1_bf16<<<grid, kThreads, kSmemBytes, st>>>(a, m, tmap ? 1 : 0);
   return cudaGetLastError();
+}
+
+bool encode_sensor_tmap(CUtensorMap* map, const float* E, int W, int H) {
+  // rows must be a multiple of 16 bytes and hold the 40-wide box; planes of 6 rows at least
+  if ((W & 3) != 0 || W < kStageW || H < kHaloH) return false;
+  if ((reinterpret_cast<uintptr_t>(E) & 15) != 0) return false;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+      cudaGetLastError();
+      return false;
+    }
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, 6};
+  const cuuint64_t strides[2] = {(cuuint64_t)W * 4, (cuuint64_t)W * (cuuint64_t)H * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)kStageW, (cuuint32_t)kHaloH, 6};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(E), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 }  // namespace coral
