@@ -32,11 +32,23 @@ __host__ __device__ inline int net32_stride(int H) {
 
 // ---- BF16 tensor-core net blob (one per slot; byte image of the shared-memory operands) --
 // [0, n1*128)         W1 (or W for hidden = 0): n1 rows of 64 bf16 (K-major, 128-byte rows,
-//                     16-byte chunks XOR-swizzled by row & 7), K index = 6*rank + channel,
-//                     K = 54 holds the layer-1 bias (the A operand carries 1.0 there).
+//                     16-byte chunks XOR-swizzled by row & 7). K slot k = 8p + c holds input
+//                     (rank p, channel c) for p < 8, c < 6; the spare slots 8p + 6, 8p + 7 of
+//                     p = 0, 1, 2 hold rank 8's channels 2p, 2p + 1; slot 30 holds the layer-1
+//                     bias (the A operand carries 1.0 there); every other slot is zero. Each
+//                     16-byte chunk of an input row is then one cell record (6 channels of
+//                     one neighbour) plus one word of rank 8 / bias.
 // [n1*128, +2048)     W2: 16 rows x 64 bf16 (10 used), same swizzle; absent for hidden = 0.
 // then                b2 (or nothing for hidden = 0): 16 float32.
 __host__ __device__ inline int bf16_n1(int H) { return H ? H : 16; }
+// Input index (6 * rank + channel) held by K slot k of the tensor-core input row, 54 for the
+// bias slot, -1 for a zero slot.
+__host__ __device__ inline int bf16_kslot_input(int k) {
+  const int p = k >> 3, c = k & 7;
+  if (c < 6) return 6 * p + c;
+  if (p < 3) return 48 + 2 * p + (c - 6);
+  return k == 30 ? kIn : -1;
+}
 __host__ __device__ inline int bf16_w2_off(int H) { return bf16_n1(H) * 128; }
 __host__ __device__ inline int bf16_b2_off(int H) { return H ? bf16_w2_off(H) + 16 * 128 : bf16_w2_off(H); }
 __host__ __device__ inline int bf16_blob_bytes(int H) {

@@ -261,28 +261,25 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
           }
         }
       }
-      // this cell's input row: 9 records in kernel-rank order, 1.0 at K = 54, swizzled
-      if (first_round) {
-        uint32_t wv[32];
+      // this cell's input row: chunk p = the record of kernel rank p (p < 8) whose spare 4th
+      // word carries rank 8's channels (p < 3) or the bias 1.0 (p = 3); 128-byte swizzle.
+      // Rows of cells outside the grid are left as they are: their outputs are discarded.
+      if (first_round && valid) {
+        const uint32_t c_s = rec_s + hc * 16;
+        const unsigned long long offs = r == 0 ? rank_offsets(0) : r == 1 ? rank_offsets(1)
+                                      : r == 2 ? rank_offsets(2) : rank_offsets(3);
+        const uint4 r8 = tc::lds128(c_s + (int)(int8_t)(uint8_t)(offs >> 56) * 16);
+        const uint32_t row_s = a_s + tid * 128;
+        const uint32_t t7 = tid & 7;
+        uint4 rc = tc::lds128(c_s);
+        tc::sts128(row_s + ((0u ^ t7) << 4), rc.x, rc.y, rc.z, r8.x);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) wv[i] = 0u;
-        if (valid) {
-          const uint32_t c_s = rec_s + hc * 16;
-          uint4 rc = tc::lds128(c_s);
-          wv[0] = rc.x; wv[1] = rc.y; wv[2] = rc.z;
-          const unsigned long long offs = r == 0 ? rank_offsets(0) : r == 1 ? rank_offsets(1)
-                                        : r == 2 ? rank_offsets(2) : rank_offsets(3);
-#pragma unroll
-          for (int p = 1; p < 9; ++p) {
-            const int off = (int)(int8_t)(uint8_t)(offs >> (8 * (p - 1)));
-            rc = tc::lds128(c_s + off * 16);
-            wv[3 * p] = rc.x; wv[3 * p + 1] = rc.y; wv[3 * p + 2] = rc.z;
-          }
-          wv[27] = 0x3F80u;                  // bf16 1.0 at K = 54 (layer-1 bias), 0 at K = 55
+        for (int p = 1; p < 8; ++p) {
+          const int off = (int)(int8_t)(uint8_t)(offs >> (8 * (p - 1)));
+          rc = tc::lds128(c_s + off * 16);
+          const uint32_t w4 = p == 1 ? r8.y : (p == 2 ? r8.z : (p == 3 ? 0x3F80u : 0u));
+          tc::sts128(row_s + (((uint32_t)p ^ t7) << 4), rc.x, rc.y, rc.z, w4);
         }
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-          tc::sts128(row_s + ((c ^ (tid & 7)) << 4), wv[4 * c], wv[4 * c + 1], wv[4 * c + 2], wv[4 * c + 3]);
       }
       tc::fence_proxy_async();
       __syncthreads();

@@ -126,7 +126,8 @@ __global__ void __launch_bounds__(256) k_bf16_pack(GenomeArgs g, const int32_t* 
     for (int c = threadIdx.x; c < n1 * 64; c += blockDim.x) {
       const int row = c >> 6, k = c & 63;
       float v = 0.0f;
-      if (row < rows1) v = k < kIn ? rec[row * 56 + k] : (k == kIn ? rec[net32_b1(H) + row] : 0.0f);
+      const int i = bf16_kslot_input(k);
+      if (row < rows1 && i >= 0) v = i < kIn ? rec[row * 56 + i] : rec[net32_b1(H) + row];
       *reinterpret_cast<__nv_bfloat16*>(blob + swz(row, k)) = __float2bfloat16_rn(v);
     }
     if (H) {
