@@ -206,6 +206,33 @@ int coral_get_step(const coral_substrate* s, int64_t* t);
 int coral_launch_config(const coral_substrate* s, int32_t* grid_pass1, int32_t* grid_pass2,
                         int32_t* sms);
 
+/*
+ * Batched stepping of many independent worlds (many substrates in one launch per pass, the
+ * per-step launch sequence replayed as a CUDA graph). All worlds: BF16 path, the same hidden
+ * size, radiation off, a genome table loaded, the current CUDA device. The CTAs of each launch
+ * are divided among the worlds in proportion to their sizes (each CTA works on one world), so a
+ * world's result is bit-identical to stepping it alone. The batch has its own stream; before
+ * each coral_batch_step it waits for work already enqueued on the worlds' streams, and the
+ * worlds' streams wait for the batch's steps, so per-world calls (reads, loads) stay ordered.
+ * The substrates stay owned by the caller and must outlive the batch.
+ * Errors: E_INVALID (mixed hidden sizes / paths / devices, radiation on), E_STATE (no genome
+ * table), E_OOM, E_CUDA.
+ */
+typedef struct coral_batch coral_batch;
+int coral_batch_create(coral_substrate* const* worlds, int32_t n, coral_batch** out);
+int coral_batch_destroy(coral_batch* b);
+/* Enqueues n_steps steps of every world (each a replay of one captured CUDA graph). */
+int coral_batch_step(coral_batch* b, int32_t n_steps);
+/* Same, with a CUDA event pair around every step: step_ms[n_steps] (host). Synchronises. */
+int coral_batch_step_timed(coral_batch* b, int32_t n_steps, float* step_ms);
+/*
+ * Autotuner: times trial_steps steps (after one warm-up) for each candidate launch shape —
+ * pass-1 CTAs per SM in {2, 3, 4, 5} x pass-2 CTAs per SM in {1, 2, 3} — keeps the fastest and
+ * restores every world's state and step index afterwards. choice: [3] = {pass-1 CTAs per SM,
+ * pass-2 CTAs per SM, best step time in microseconds} (may be NULL). Synchronises.
+ */
+int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* choice);
+
 /* Waits for the stream and returns the first latched device-side error, if any. */
 int coral_sync(coral_substrate* s);
 

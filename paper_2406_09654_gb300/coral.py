@@ -79,6 +79,11 @@ SIGNATURES = {
     "coral_last_error": (ctypes.c_char_p, [_VP]),
     "coral_net_floats": (_I32, [_I32]),
     "coral_bucket_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _VP]),
+    "coral_batch_create": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(_VP)]),
+    "coral_batch_destroy": (ctypes.c_int, [_VP]),
+    "coral_batch_step": (ctypes.c_int, [_VP, _I32]),
+    "coral_batch_step_timed": (ctypes.c_int, [_VP, _I32, _VP]),
+    "coral_batch_tune": (ctypes.c_int, [_VP, _I32, _VP]),
     "coral_bucket_noalloc_last_error": (ctypes.c_char_p, []),
 }
 
@@ -340,3 +345,52 @@ def bucket_noalloc(G, capacity, counts, perm, stream=None):
                                     _ptr(perm)[0], sp)
     if rc != OK:
         raise CoralError(rc, lib().coral_bucket_noalloc_last_error().decode())
+
+
+class Batch:
+    """Many substrates stepped together: one launch per pass over all worlds, each step a CUDA
+    graph replay (see coral_batch_create in include/coral.h). The substrates stay owned by
+    the caller and must outlive the batch."""
+
+    def __init__(self, substrates):
+        self.worlds = list(substrates)
+        arr = (ctypes.c_void_p * len(self.worlds))(*[s.h for s in self.worlds])
+        h = ctypes.c_void_p()
+        rc = lib().coral_batch_create(arr, len(self.worlds), ctypes.byref(h))
+        if rc != OK:
+            raise CoralError(rc, lib().coral_last_error(None).decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise CoralError(rc, lib().coral_last_error(None).decode())
+
+    def step(self, n=1):
+        self._check(lib().coral_batch_step(self.h, int(n)))
+
+    def step_timed(self, n=1):
+        ms = np.empty(int(n), np.float32)
+        self._check(lib().coral_batch_step_timed(self.h, int(n), ms.ctypes.data))
+        return ms
+
+    def tune(self, trial_steps=3):
+        c = np.zeros(3, np.int32)
+        self._check(lib().coral_batch_tune(self.h, int(trial_steps), c.ctypes.data))
+        return {"pass1_ctas_per_sm": int(c[0]), "pass2_ctas_per_sm": int(c[1]), "step_us": int(c[2])}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().coral_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

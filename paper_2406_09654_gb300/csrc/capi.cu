@@ -3,6 +3,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 #include <string>
 #include <vector>
@@ -112,6 +113,8 @@ StepArgs step_args(const coral_substrate* s) {
   a.fma_cutoff = s->p.fma_cutoff;
   a.max_mma_genomes = s->p.max_mma_genomes;
   a.status = s->status;
+  a.day_period = s->p.day_period;
+  a.step_dev = nullptr;
   return a;
 }
 
@@ -537,3 +540,357 @@ int coral_sync(coral_substrate* s) {
 const char* coral_last_error(const coral_substrate* s) { return s ? s->err.c_str() : g_err.c_str(); }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Batched stepping
+// ---------------------------------------------------------------------------------------------
+struct coral_batch {
+  std::vector<coral_substrate*> worlds;
+  cudaStream_t stream = nullptr;
+  int sms = 0;
+  int n = 0;
+  void* dmem = nullptr;          // one device block for the tables
+  StepArgs* d_args = nullptr;    // [2][n]
+  int* d_part = nullptr;         // cta_world1 | first1 | ctas1 | cta_world2 | first2 | ctas2
+  coral_stats** d_rings = nullptr;
+  long long* d_steps = nullptr;
+  int cps1 = 5, cps2 = 3;        // CTAs per SM of pass 1 / pass 2
+  int grid1 = 0, grid2 = 0;
+  int max_grid = 0;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaEvent_t ev = nullptr;
+  long long steps_done = 0;      // parity of the batch (world w's current buffer = cur0[w] ^ parity)
+  std::vector<int> cur0;
+  std::string err;
+};
+
+namespace {
+
+int bfail(coral_batch* b, int code, const std::string& m) {
+  if (b) b->err = m;
+  g_err = m;
+  return code;
+}
+
+#define BCK(b, call)                                                                        \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return bfail((b), e_ == cudaErrorMemoryAllocation ? CORAL_E_OOM : CORAL_E_CUDA, \
+                                        std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Splits `grid` CTAs among the worlds in proportion to `work` (largest remainder, at least one
+// CTA each); fills cta_world [grid], first [n], ctas [n]. Returns the grid actually used.
+int partition(const std::vector<long long>& work, int grid, std::vector<int>& cta_world, std::vector<int>& first,
+              std::vector<int>& ctas) {
+  const int n = (int)work.size();
+  if (grid < n) grid = n;
+  long long total = 0;
+  for (long long w : work) total += w;
+  ctas.assign(n, 1);
+  int left = grid - n;
+  std::vector<std::pair<double, int>> rem;
+  int given = 0;
+  for (int i = 0; i < n; ++i) {
+    const double share = (double)left * (double)work[i] / (double)(total ? total : 1);
+    const int k = (int)share;
+    ctas[i] += k;
+    given += k;
+    rem.push_back({share - k, i});
+  }
+  std::stable_sort(rem.begin(), rem.end(), [](const std::pair<double, int>& a, const std::pair<double, int>& b) {
+    return a.first > b.first;
+  });
+  for (int i = 0; i < left - given; ++i) ctas[rem[i].second] += 1;
+  first.assign(n, 0);
+  cta_world.clear();
+  for (int i = 0; i < n; ++i) {
+    first[i] = (int)cta_world.size();
+    for (int k = 0; k < ctas[i]; ++k) cta_world.push_back(i);
+  }
+  return (int)cta_world.size();
+}
+
+BatchTable table_of(const coral_batch* b) {
+  BatchTable t;
+  t.n = b->n;
+  t.args = b->d_args;
+  const int g = b->max_grid;
+  t.cta_world1 = b->d_part;
+  t.world_first1 = b->d_part + g;
+  t.world_ctas1 = b->d_part + g + b->n;
+  t.cta_world2 = b->d_part + g + 2 * b->n;
+  t.world_first2 = b->d_part + 2 * g + 2 * b->n;
+  t.world_ctas2 = b->d_part + 2 * g + 3 * b->n;
+  t.rings = b->d_rings;
+  t.steps = b->d_steps;
+  return t;
+}
+
+// Launch shapes for the current cps1 / cps2, partition tables and the two graphs.
+int batch_configure(coral_batch* b) {
+  std::vector<long long> tiles, cells;
+  for (coral_substrate* s : b->worlds) {
+    tiles.push_back((long long)((s->W + 31) / 32) * ((s->H + 3) / 4));
+    cells.push_back(s->N);
+  }
+  std::vector<int> cw1, f1, c1, cw2, f2, c2;
+  b->grid1 = partition(tiles, b->cps1 * b->sms, cw1, f1, c1);
+  b->grid2 = partition(cells, b->cps2 * b->sms, cw2, f2, c2);
+  if (b->grid1 > b->max_grid || b->grid2 > b->max_grid) return bfail(b, CORAL_E_INVALID, "launch shape too large");
+  for (int i = 0; i < b->n; ++i)
+    if (c1[i] > kMaxPartials || c2[i] > kMaxPartials) return bfail(b, CORAL_E_INVALID, "too many CTAs for one world");
+  std::vector<int> part(4 * (size_t)b->max_grid + 6 * (size_t)b->n, 0);
+  const int g = b->max_grid;
+  std::copy(cw1.begin(), cw1.end(), part.begin());
+  std::copy(f1.begin(), f1.end(), part.begin() + g);
+  std::copy(c1.begin(), c1.end(), part.begin() + g + b->n);
+  std::copy(cw2.begin(), cw2.end(), part.begin() + g + 2 * b->n);
+  std::copy(f2.begin(), f2.end(), part.begin() + 2 * g + 2 * b->n);
+  std::copy(c2.begin(), c2.end(), part.begin() + 2 * g + 3 * b->n);
+  BCK(b, cudaMemcpyAsync(b->d_part, part.data(), sizeof(int) * (2 * (size_t)g + 4 * (size_t)b->n), cudaMemcpyHostToDevice,
+                         b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  BCK(b, prepare_pass1_bf16_batch());
+  const BatchTable t = table_of(b);
+  for (int p = 0; p < 2; ++p) {
+    if (b->graph[p]) {
+      cudaGraphExecDestroy(b->graph[p]);
+      b->graph[p] = nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = launch_pass1_bf16_batch(t, p, b->grid1, b->stream);
+    if (e == cudaSuccess) e = launch_pass2_batch(t, p, b->grid2, b->stream);
+    if (e == cudaSuccess) e = launch_stats_batch(t, b->stream);
+    const cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return bfail(b, CORAL_E_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&b->graph[p], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfail(b, CORAL_E_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  }
+  return CORAL_OK;
+}
+
+// Orders the batch stream after the worlds' streams, refreshes the device step indices.
+int batch_enter(coral_batch* b) {
+  for (coral_substrate* s : b->worlds) {
+    BCK(b, cudaEventRecord(b->ev, s->stream));
+    BCK(b, cudaStreamWaitEvent(b->stream, b->ev, 0));
+  }
+  std::vector<long long> t(b->n);
+  for (int i = 0; i < b->n; ++i) t[i] = b->worlds[i]->t;
+  BCK(b, cudaMemcpyAsync(b->d_steps, t.data(), sizeof(long long) * b->n, cudaMemcpyHostToDevice, b->stream));
+  return CORAL_OK;
+}
+
+// Orders the worlds' streams after the batch stream; advances the worlds' bookkeeping.
+int batch_leave(coral_batch* b, int n_steps) {
+  BCK(b, cudaEventRecord(b->ev, b->stream));
+  for (coral_substrate* s : b->worlds) {
+    BCK(b, cudaStreamWaitEvent(s->stream, b->ev, 0));
+    s->cur ^= (n_steps & 1);
+    s->t += n_steps;
+  }
+  b->steps_done += n_steps;
+  return CORAL_OK;
+}
+
+// The worlds' step arguments for both parities relative to their current buffers.
+int batch_upload_args(coral_batch* b) {
+  std::vector<StepArgs> args(2 * (size_t)b->n);
+  for (int p = 0; p < 2; ++p)
+    for (int i = 0; i < b->n; ++i) {
+      coral_substrate* s = b->worlds[i];
+      const int save = s->cur;
+      s->cur = save ^ p;
+      StepArgs a = step_args(s);
+      s->cur = save;
+      a.step_dev = b->d_steps + i;
+      args[(size_t)p * b->n + i] = a;
+    }
+  BCK(b, cudaMemcpyAsync(b->d_args, args.data(), sizeof(StepArgs) * args.size(), cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaStreamSynchronize(b->stream));
+  return CORAL_OK;
+}
+
+}  // namespace
+
+extern "C" int coral_batch_create(coral_substrate* const* worlds, int32_t n, coral_batch** out) {
+  if (!worlds || !out || n < 1) return bfail(nullptr, CORAL_E_INVALID, "bad arguments");
+  *out = nullptr;
+  coral_batch* b = nullptr;
+  try {
+    b = new coral_batch();
+  } catch (...) {
+    return bfail(nullptr, CORAL_E_OOM, "host allocation failed");
+  }
+  b->n = n;
+  int rc = CORAL_OK;
+  do {
+    int dev = -1;
+    for (int i = 0; i < n; ++i) {
+      coral_substrate* s = worlds[i];
+      if (!s) { rc = bfail(b, CORAL_E_INVALID, "NULL world"); break; }
+      if (s->p.path != CORAL_NET_BF16_GROUPED) { rc = bfail(b, CORAL_E_INVALID, "batched worlds use the BF16 path"); break; }
+      if (s->p.hidden != worlds[0]->p.hidden) { rc = bfail(b, CORAL_E_INVALID, "batched worlds share one hidden size"); break; }
+      if (s->p.radiation_every > 0) { rc = bfail(b, CORAL_E_INVALID, "radiation is not batched"); break; }
+      if (!s->genomes_loaded) { rc = bfail(b, CORAL_E_STATE, "a world has no genome table"); break; }
+      if (dev >= 0 && s->device != dev) { rc = bfail(b, CORAL_E_INVALID, "worlds on different devices"); break; }
+      dev = s->device;
+      b->worlds.push_back(s);
+    }
+    if (rc) break;
+    b->sms = worlds[0]->sms;
+    b->max_grid = std::max(5 * b->sms, n) + 8;
+    cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
+    const size_t bytes = sizeof(StepArgs) * 2 * (size_t)n + 256 + sizeof(int) * (4 * (size_t)b->max_grid + 6 * (size_t)n) +
+                         256 + sizeof(coral_stats*) * (size_t)n + 256 + sizeof(long long) * (size_t)n + 256;
+    if (e == cudaSuccess) e = cudaMalloc(&b->dmem, bytes);
+    if (e != cudaSuccess) { rc = bfail(b, e == cudaErrorMemoryAllocation ? CORAL_E_OOM : CORAL_E_CUDA, cudaGetErrorString(e)); break; }
+    char* p = static_cast<char*>(b->dmem);
+    auto carve = [&](size_t nbytes) {
+      char* q = p;
+      p += (nbytes + 255) & ~(size_t)255;
+      return q;
+    };
+    b->d_args = reinterpret_cast<StepArgs*>(carve(sizeof(StepArgs) * 2 * (size_t)n));
+    b->d_part = reinterpret_cast<int*>(carve(sizeof(int) * (4 * (size_t)b->max_grid + 6 * (size_t)n)));
+    b->d_rings = reinterpret_cast<coral_stats**>(carve(sizeof(coral_stats*) * (size_t)n));
+    b->d_steps = reinterpret_cast<long long*>(carve(sizeof(long long) * (size_t)n));
+    std::vector<coral_stats*> rings(n);
+    for (int i = 0; i < n; ++i) rings[i] = worlds[i]->ring;
+    if ((e = cudaMemcpy(b->d_rings, rings.data(), sizeof(coral_stats*) * n, cudaMemcpyHostToDevice)) != cudaSuccess) {
+      rc = bfail(b, CORAL_E_CUDA, cudaGetErrorString(e));
+      break;
+    }
+    for (coral_substrate* s : b->worlds) cudaStreamSynchronize(s->stream);
+    if ((rc = batch_upload_args(b)) != CORAL_OK) break;
+    rc = batch_configure(b);
+  } while (0);
+  if (rc != CORAL_OK) {
+    coral_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return CORAL_OK;
+}
+
+extern "C" int coral_batch_destroy(coral_batch* b) {
+  if (!b) return CORAL_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (int p = 0; p < 2; ++p)
+    if (b->graph[p]) cudaGraphExecDestroy(b->graph[p]);
+  if (b->ev) cudaEventDestroy(b->ev);
+  if (b->dmem) cudaFree(b->dmem);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return CORAL_OK;
+}
+
+namespace {
+int batch_run(coral_batch* b, int32_t n_steps, float* step_ms) {
+  if (!b) return bfail(nullptr, CORAL_E_INVALID, "NULL batch");
+  if (n_steps < 0) return bfail(b, CORAL_E_INVALID, "n_steps must be >= 0");
+  if (n_steps == 0) return CORAL_OK;
+  int rc = batch_upload_args(b);          // worlds may have been reloaded or stepped alone
+  if (rc) return rc;
+  if ((rc = batch_enter(b)) != CORAL_OK) return rc;
+  std::vector<cudaEvent_t> ev;
+  if (step_ms) {
+    ev.resize(n_steps + 1);
+    for (auto& e : ev) BCK(b, cudaEventCreate(&e));
+    BCK(b, cudaEventRecord(ev[0], b->stream));
+  }
+  for (int i = 0; i < n_steps; ++i) {
+    BCK(b, cudaGraphLaunch(b->graph[i & 1], b->stream));
+    if (step_ms) BCK(b, cudaEventRecord(ev[i + 1], b->stream));
+  }
+  if ((rc = batch_leave(b, n_steps)) != CORAL_OK) return rc;
+  if (step_ms) {
+    BCK(b, cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < n_steps; ++i) cudaEventElapsedTime(&step_ms[i], ev[i], ev[i + 1]);
+    for (auto& e : ev) cudaEventDestroy(e);
+  }
+  return CORAL_OK;
+}
+}  // namespace
+
+extern "C" int coral_batch_step(coral_batch* b, int32_t n_steps) { return batch_run(b, n_steps, nullptr); }
+
+extern "C" int coral_batch_step_timed(coral_batch* b, int32_t n_steps, float* step_ms) {
+  if (!step_ms) return bfail(b, CORAL_E_INVALID, "step_ms is NULL");
+  return batch_run(b, n_steps, step_ms);
+}
+
+extern "C" int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* choice) {
+  if (!b) return bfail(nullptr, CORAL_E_INVALID, "NULL batch");
+  if (trial_steps < 1) return bfail(b, CORAL_E_INVALID, "trial_steps must be >= 1");
+  // save every world's current state and step index
+  std::vector<void*> saved(b->n, nullptr);
+  std::vector<long long> t0(b->n);
+  std::vector<int> c0(b->n);
+  for (int i = 0; i < b->n; ++i) {
+    coral_substrate* s = b->worlds[i];
+    cudaStreamSynchronize(s->stream);
+    t0[i] = s->t;
+    c0[i] = s->cur;
+    const size_t bytes = (size_t)s->N * 29;
+    if (cudaMalloc(&saved[i], bytes) != cudaSuccess) {
+      for (void* q : saved) if (q) cudaFree(q);
+      cudaGetLastError();
+      return bfail(b, CORAL_E_OOM, "no memory to save the states for tuning");
+    }
+    char* q = static_cast<char*>(saved[i]);
+    const Planes& d = s->st[s->cur];
+    cudaMemcpy(q, d.E, (size_t)s->N * 24, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(q + (size_t)s->N * 24, d.G, (size_t)s->N * 4, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(q + (size_t)s->N * 28, d.R, (size_t)s->N, cudaMemcpyDeviceToDevice);
+  }
+  const int c1s[4] = {2, 3, 4, 5}, c2s[3] = {1, 2, 3};
+  float best = 1e30f;
+  int b1 = b->cps1, b2 = b->cps2, rc = CORAL_OK;
+  std::vector<float> ms(trial_steps + 1);
+  for (int i1 = 0; i1 < 4 && rc == CORAL_OK; ++i1)
+    for (int i2 = 0; i2 < 3 && rc == CORAL_OK; ++i2) {
+      b->cps1 = c1s[i1];
+      b->cps2 = c2s[i2];
+      if ((rc = batch_configure(b)) != CORAL_OK) break;
+      if ((rc = batch_run(b, trial_steps + 1, ms.data())) != CORAL_OK) break;
+      float tot = 0;
+      for (int k = 1; k <= trial_steps; ++k) tot += ms[k];
+      if (tot < best) {
+        best = tot;
+        b1 = c1s[i1];
+        b2 = c2s[i2];
+      }
+    }
+  // restore
+  cudaStreamSynchronize(b->stream);
+  for (int i = 0; i < b->n; ++i) {
+    coral_substrate* s = b->worlds[i];
+    cudaStreamSynchronize(s->stream);
+    s->cur = c0[i];
+    s->t = t0[i];
+    const char* q = static_cast<const char*>(saved[i]);
+    const Planes& d = s->st[s->cur];
+    cudaMemcpy(d.E, q, (size_t)s->N * 24, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(d.G, q + (size_t)s->N * 24, (size_t)s->N * 4, cudaMemcpyDeviceToDevice);
+    cudaMemcpy(d.R, q + (size_t)s->N * 28, (size_t)s->N, cudaMemcpyDeviceToDevice);
+    cudaFree(saved[i]);
+  }
+  if (rc != CORAL_OK) return rc;
+  b->cps1 = b1;
+  b->cps2 = b2;
+  if ((rc = batch_configure(b)) != CORAL_OK) return rc;
+  if (choice) {
+    choice[0] = b1;
+    choice[1] = b2;
+    choice[2] = (int32_t)(1000.0f * best / trial_steps);
+  }
+  return CORAL_OK;
+}

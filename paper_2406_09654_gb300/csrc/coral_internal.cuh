@@ -98,6 +98,24 @@ struct StepArgs {
   int fma_cutoff;
   int max_mma_genomes;
   int* status;
+  int day_period;
+  const long long* step_dev;   // batched stepping: this world's step index on the device (day/night
+                               // is taken from it); NULL: use is_day
+};
+
+// Batched stepping of many worlds (same hidden size, BF16 path): the CTAs of each launch are
+// split among the worlds (contiguous CTA ranges), every CTA works on one world only.
+struct BatchTable {
+  int n;                          // worlds
+  const StepArgs* args;           // [2][n]: parity p = batch step count & 1
+  const int* cta_world1;          // pass 1: world of each CTA
+  const int* world_first1;        //   first CTA of each world
+  const int* world_ctas1;         //   CTAs of each world
+  const int* cta_world2;          // pass 2: same
+  const int* world_first2;
+  const int* world_ctas2;
+  coral_stats* const* rings;      // [n] stats rings
+  long long* steps;               // [n] step index of each world (advanced by the stats kernel)
 };
 
 // ---- Philox4x32-10 (Salmon et al., SC'11), written for the device -----------------------
@@ -174,6 +192,10 @@ bool encode_sensor_tmap(CUtensorMap* map, const float* E, int W, int H);
 cudaError_t launch_pass2(const StepArgs& a, cudaStream_t st, int grid);
 cudaError_t launch_stats(const StepArgs& a, int n_part1, int n_part2, long long t,
                          coral_stats* ring, cudaStream_t st);
+cudaError_t prepare_pass1_bf16_batch();   // kernel attributes, once before any capture
+cudaError_t launch_pass1_bf16_batch(const BatchTable& b, int parity, int grid, cudaStream_t st);
+cudaError_t launch_pass2_batch(const BatchTable& b, int parity, int grid, cudaStream_t st);
+cudaError_t launch_stats_batch(const BatchTable& b, cudaStream_t st);
 int pass1_fp32_grid(int sms);
 int pass1_bf16_grid(int sms);
 int pass2_grid(int sms);

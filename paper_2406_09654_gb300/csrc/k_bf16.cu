@@ -91,8 +91,10 @@ __device__ __forceinline__ void issue_halo(const StepArgs& a, int y0, int col_a,
   tc::cp_async_commit();
 }
 
-__global__ void __launch_bounds__(kThreads, kCtasPerSm)
-    k_pass1_bf16(const StepArgs a, const __grid_constant__ CUtensorMap tmap, const int use_tma) {
+// One CTA's share of pass 1 for one world: CTA `cta` of `ncta` takes a contiguous run of tiles;
+// its partial sums go to a.part1[cta]. tmap: TMA descriptor (use_tma != 0) or unused.
+__device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtensorMap* tmap, const int use_tma,
+                                                const int cta, const int ncta) {
   extern __shared__ uint8_t smem_raw[];
   const uint32_t raw_s = tc::smem_u32(smem_raw);
   const uint32_t base_s = (raw_s + 1023u) & ~1023u;
@@ -140,8 +142,8 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
   const int tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (Hh + kTileH - 1) / kTileH;
   const int n_tiles = tiles_x * tiles_y;
   // a contiguous run of tiles per CTA: neighbouring tiles share halo rows (L2) and genomes
-  const int per = (n_tiles + gridDim.x - 1) / gridDim.x;
-  const int t_begin = blockIdx.x * per;
+  const int per = (n_tiles + ncta - 1) / ncta;
+  const int t_begin = cta * per;
   const int t_end = t_begin + per < n_tiles ? t_begin + per : n_tiles;
   int g_next = -1, r_next = 0;
   const bool small_w = W < kHaloW;
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
       if (tid == 0) {
         tc::fence_proxy_async();                       // earlier generic accesses of the buffer
         tc::mbar_expect_tx(&halo_bar[b], kStageBytes);
-        tc::tma_load_3d(dst, &tmap, x0 - 4, y0 - 1, 0, &halo_bar[b]);
+        tc::tma_load_3d(dst, tmap, x0 - 4, y0 - 1, 0, &halo_bar[b]);
       }
       tma_pending = b;
     } else {
@@ -405,12 +407,23 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
       for (int k = 0; k < 4; ++k) p.s[2 + k] += red_s[w][k];
       p.c[0] += red_c[w];
     }
-    a.part1[blockIdx.x] = p;
+    a.part1[cta] = p;
   }
   if (warp == 0) {
     tc::tc_fence_after();
     tc::tmem_dealloc(tmem, kTmemCols);
   }
+}
+
+__global__ void __launch_bounds__(kThreads, kCtasPerSm)
+    k_pass1_bf16(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tmap, const int use_tma) {
+  pass1_bf16_body(a, &tmap, use_tma, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16_batch(const __grid_constant__ BatchTable bt,
+                                                                          const int parity) {
+  const int w = bt.cta_world1[blockIdx.x];
+  pass1_bf16_body(bt.args[parity * bt.n + w], nullptr, 0, blockIdx.x - bt.world_first1[w], bt.world_ctas1[w]);
 }
 
 }  // namespace
@@ -451,6 +464,19 @@ int pass1_bf16_grid(int sms) {
   if (per_sm < 1) return 0;
   const int g = per_sm * sms;
   return g > kMaxPartials ? kMaxPartials : g;
+}
+
+cudaError_t prepare_pass1_bf16_batch() {
+  cudaError_t e = cudaFuncSetAttribute(k_pass1_bf16_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_pass1_bf16_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  return e;
+}
+
+cudaError_t launch_pass1_bf16_batch(const BatchTable& b, int parity, int grid, cudaStream_t st) {
+  k_pass1_bf16_batch<<<grid, kThreads, kSmemBytes, st>>>(b, parity);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pass1_bf16(const StepArgs& a, const CUtensorMap* tmap, cudaStream_t st, int grid) {

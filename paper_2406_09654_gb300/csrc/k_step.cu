@@ -27,7 +27,7 @@ __device__ __forceinline__ void warp_accumulate(float v, double& acc) {
 // Combines the lane-0 accumulators of all warps of the block in warp order.
 template <int NS, int NC>
 __device__ void block_partial(const double (&s)[NS], const long long (&c)[NC], Partial* out,
-                              int s_first, int c_first) {
+                              int s_first, int c_first, int slot) {
   __shared__ double ss[32][6];
   __shared__ long long sc[32][2];
   const int w = threadIdx.x >> 5;
@@ -42,7 +42,7 @@ __device__ void block_partial(const double (&s)[NS], const long long (&c)[NC], P
       for (int k = 0; k < NS; ++k) p.s[s_first + k] += ss[i][k];
       for (int k = 0; k < NC; ++k) p.c[c_first + k] += sc[i][k];
     }
-    out[blockIdx.x] = p;
+    out[slot] = p;
   }
 }
 
@@ -146,17 +146,26 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1_fp32(const StepArgs a) {
     const int ex = warp_sum_i(valid && o.xdir != kNoExplore ? 1 : 0);
     if ((threadIdx.x & 31) == 0) accX[0] += ex;
   }
-  block_partial<4, 1>(accC, accX, a.part1, 2, 0);
+  block_partial<4, 1>(accC, accX, a.part1, 2, 0, blockIdx.x);
 }
 
-// Pass 2: exploration resolve and takeover, energy flow, day/night (one thread per cell).
-__global__ void __launch_bounds__(kP2Threads) k_pass2(const StepArgs a) {
+// Day or night for this step (batched stepping reads the step index from the device).
+__device__ __forceinline__ bool is_day_now(const StepArgs& a) {
+  if (!a.step_dev) return a.is_day != 0;
+  const long long t = *a.step_dev;
+  return (t % a.day_period) * 2 < a.day_period;
+}
+
+// Pass 2: exploration resolve and takeover, energy flow, day/night (one thread per cell);
+// CTA `cta` of `ncta` strides over the world's cells, partial sums to a.part2[cta].
+__device__ __forceinline__ void pass2_body(const StepArgs& a, const int cta, const int ncta) {
   const int W = a.W, H = a.H;
   const long long N = a.N;
+  const bool day = is_day_now(a);
   double acc[2] = {0, 0};
   long long accT[1] = {0};
-  const long long stride = (long long)gridDim.x * kP2Threads;
-  for (long long base = (long long)blockIdx.x * kP2Threads; base < N; base += stride) {
+  const long long stride = (long long)ncta * kP2Threads;
+  for (long long base = (long long)cta * kP2Threads; base < N; base += stride) {
     const long long j = base + threadIdx.x;
     const bool valid = j < N;
     float E3 = 0.0f, I2 = 0.0f;
@@ -193,7 +202,7 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(const StepArgs a) {
       }
       const float inflow = ((qn[0] + qn[1]) + qn[2]) + qn[3];
       const float E2 = me.x + a.cur.I[j] * inflow;
-      E3 = a.is_day ? E2 + a.e_day : E2 - a.e_night * E2;
+      E3 = day ? E2 + a.e_day : E2 - a.e_night * E2;
       a.nxt.E[j] = E3;
       a.nxt.I[j] = I2;
       a.nxt.G[j] = g;
@@ -204,20 +213,21 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(const StepArgs a) {
     const int tk = warp_sum_i(take ? 1 : 0);
     if ((threadIdx.x & 31) == 0) accT[0] += tk;
   }
-  block_partial<2, 1>(acc, accT, a.part2, 0, 1);
+  block_partial<2, 1>(acc, accT, a.part2, 0, 1, cta);
 }
 
 // Pass 2 for rows that are a multiple of 4 cells wide: each thread resolves 4 consecutive cells
 // of one row with 16-byte loads of the pass-1 buffers (same per-cell arithmetic and order as
-// k_pass2).
-__global__ void __launch_bounds__(kP2Threads) k_pass2_x4(const StepArgs a) {
+// pass2_body).
+__device__ __forceinline__ void pass2_x4_body(const StepArgs& a, const int cta, const int ncta) {
   const int W = a.W, H = a.H;
   const int cpr = W >> 2;                       // chunks per row
   const int n_chunks = cpr * H;
+  const bool day = is_day_now(a);
   double acc[2] = {0, 0};
   long long accT[1] = {0};
-  const int stride = gridDim.x * kP2Threads;
-  for (int base = blockIdx.x * kP2Threads; base < n_chunks; base += stride) {
+  const int stride = ncta * kP2Threads;
+  for (int base = cta * kP2Threads; base < n_chunks; base += stride) {
     const int c = base + threadIdx.x;
     const bool valid = c < n_chunks;
     float e_sum = 0.0f, i_sum = 0.0f;
@@ -288,7 +298,7 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2_x4(const StepArgs a) {
         }
         const float inflow = ((nq[0] + nq[1]) + nq[2]) + nq[3];
         const float E2 = vkp[k] + vIt[k] * inflow;
-        oE[k] = a.is_day ? E2 + a.e_day : E2 - a.e_night * E2;
+        oE[k] = day ? E2 + a.e_day : E2 - a.e_night * E2;
         oI[k] = I2;
         oG[k] = g;
         oR |= r << (8 * k);
@@ -305,7 +315,25 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2_x4(const StepArgs a) {
     const int tk = warp_sum_i(takes);
     if ((threadIdx.x & 31) == 0) accT[0] += tk;
   }
-  block_partial<2, 1>(acc, accT, a.part2, 0, 1);
+  block_partial<2, 1>(acc, accT, a.part2, 0, 1, cta);
+}
+
+__global__ void __launch_bounds__(kP2Threads) k_pass2(const __grid_constant__ StepArgs a) {
+  pass2_body(a, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kP2Threads) k_pass2_x4(const __grid_constant__ StepArgs a) {
+  pass2_x4_body(a, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(kP2Threads) k_pass2_batch(const __grid_constant__ BatchTable bt, const int parity) {
+  const int w = bt.cta_world2[blockIdx.x];
+  const StepArgs& a = bt.args[parity * bt.n + w];
+  const int cta = blockIdx.x - bt.world_first2[w], ncta = bt.world_ctas2[w];
+  if ((a.W & 3) == 0 && a.W >= 8)
+    pass2_x4_body(a, cta, ncta);
+  else
+    pass2_body(a, cta, ncta);
 }
 
 // Fixed-order FP64 combination of the block partials into the stats ring.
@@ -350,6 +378,53 @@ __global__ void __launch_bounds__(256) k_stats(const Partial* p1, int n1, const 
   }
 }
 
+// Batched totals: block w combines world w's partials (pass-1 and pass-2 CTA counts of that
+// world) into its ring at its device step index, then advances the step index.
+__global__ void __launch_bounds__(256) k_stats_batch(const __grid_constant__ BatchTable bt, const int parity) {
+  const int w = blockIdx.x;
+  const StepArgs& a = bt.args[parity * bt.n + w];
+  __shared__ double ss[256][6];
+  __shared__ long long sc[256][2];
+  double s[6] = {0, 0, 0, 0, 0, 0};
+  long long c[2] = {0, 0};
+  const int n1 = bt.world_ctas1[w], n2 = bt.world_ctas2[w];
+  for (int i = threadIdx.x; i < n1; i += 256) {
+    for (int k = 2; k < 6; ++k) s[k] += a.part1[i].s[k];
+    c[0] += a.part1[i].c[0];
+  }
+  for (int i = threadIdx.x; i < n2; i += 256) {
+    s[0] += a.part2[i].s[0];
+    s[1] += a.part2[i].s[1];
+    c[1] += a.part2[i].c[1];
+  }
+  for (int k = 0; k < 6; ++k) ss[threadIdx.x][k] = s[k];
+  sc[threadIdx.x][0] = c[0];
+  sc[threadIdx.x][1] = c[1];
+  __syncthreads();
+  for (int h = 128; h; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      for (int k = 0; k < 6; ++k) ss[threadIdx.x][k] += ss[threadIdx.x + h][k];
+      sc[threadIdx.x][0] += sc[threadIdx.x + h][0];
+      sc[threadIdx.x][1] += sc[threadIdx.x + h][1];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const long long t = bt.steps[w];
+    coral_stats r;
+    r.step = t;
+    r.sum_E = ss[0][0];
+    r.sum_I = ss[0][1];
+    for (int k = 0; k < 4; ++k) r.sum_C[k] = ss[0][2 + k];
+    r.n_explore = sc[0][0];
+    r.n_takeover = sc[0][1];
+    r.n_live = -1;
+    r.n_mut = r.n_merge = r.n_born = r.n_skipped = 0;
+    bt.rings[w][t % kRing] = r;
+    bt.steps[w] = t + 1;
+  }
+}
+
 int occupancy_grid(const void* fn, int threads, size_t smem, int sms) {
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess ||
@@ -378,6 +453,16 @@ cudaError_t launch_pass2(const StepArgs& a, cudaStream_t st, int grid) {
     k_pass2_x4<<<grid, kP2Threads, 0, st>>>(a);
   else
     k_pass2<<<grid, kP2Threads, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass2_batch(const BatchTable& b, int parity, int grid, cudaStream_t st) {
+  k_pass2_batch<<<grid, kP2Threads, 0, st>>>(b, parity);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats_batch(const BatchTable& b, cudaStream_t st) {
+  k_stats_batch<<<b.n, 256, 0, st>>>(b, 0);
   return cudaGetLastError();
 }
 

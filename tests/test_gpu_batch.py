@@ -1,0 +1,90 @@
+"""Batched stepping of many worlds of different sizes (one launch per pass, CUDA graph
+replays): every world's result must be bit-identical to stepping it alone, and the autotuner
+must leave the worlds' states untouched."""
+import numpy as np
+import pytest
+
+from paper_2406_09654_gb300 import coral, worlds
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_2406_09654_gb300 import build
+    build.build()
+    coral.lib()
+
+
+def mixed_worlds(n=7, seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        W = int(rng.integers(3, 300))
+        H = int(rng.integers(3, 200))
+        g = int(rng.integers(1, min(40, W * H)))
+        out.append(worlds.make_world(width=W, height=H, n_genomes=g, hidden=32, net="cppn", seed=100 + k,
+                                     random_rotation=bool(k % 2)))
+    out.append(worlds.make_world(width=256, height=128, n_genomes=30, hidden=32, net="cppn", seed=7))
+    return out
+
+
+def test_batched_equals_alone_bit_exact():
+    ws = mixed_worlds()
+    alone = []
+    for w in ws:
+        with coral.substrate_for_world(w, coral.BF16_GROUPED) as s:
+            s.step(5)
+            alone.append((s.read_channels(), s.read_stats(4, 1)[0]))
+    subs = [coral.substrate_for_world(w, coral.BF16_GROUPED) for w in ws]
+    try:
+        with coral.Batch(subs) as b:
+            b.step(2)
+            b.step(3)
+        for (ref, st), s in zip(alone, subs):
+            got = s.read_channels()
+            for k in ref:
+                assert np.array_equal(ref[k], got[k]), k
+            bs = s.read_stats(4, 1)[0]
+            assert bs["step"] == 4 and bs["n_explore"] == st["n_explore"]
+            assert bs["sum_E"] == pytest.approx(st["sum_E"], rel=1e-12)
+            assert s.get_step() == 5
+    finally:
+        for s in subs:
+            s.close()
+
+
+def test_batch_tuner_restores_state_and_mixes_with_single_steps():
+    ws = mixed_worlds(5, seed=3)
+    subs = [coral.substrate_for_world(w, coral.BF16_GROUPED) for w in ws]
+    try:
+        with coral.Batch(subs) as b:
+            choice = b.tune(trial_steps=2)
+            assert choice["pass1_ctas_per_sm"] in (2, 3, 4, 5) and choice["pass2_ctas_per_sm"] in (1, 2, 3)
+            subs[0].step(1)                          # one world steps alone in between
+            b.step(2)
+        for w, s, extra in zip(ws, subs, [1, 0, 0, 0, 0]):
+            with coral.substrate_for_world(w, coral.BF16_GROUPED) as ref:
+                ref.step(2 + extra)
+                a, g = ref.read_channels(), s.read_channels()
+                for k in a:
+                    assert np.array_equal(a[k], g[k]), k
+    finally:
+        for s in subs:
+            s.close()
+
+
+def test_batch_rejects_mixed_configurations():
+    a = worlds.make_world(width=16, height=16, n_genomes=2, hidden=32, net="cppn", seed=1)
+    c = worlds.make_world(width=16, height=16, n_genomes=2, hidden=16, net="cppn", seed=1)
+    s1 = coral.substrate_for_world(a, coral.BF16_GROUPED)
+    s2 = coral.substrate_for_world(c, coral.BF16_GROUPED)
+    s3 = coral.substrate_for_world(a, coral.FP32_PERCELL)
+    try:
+        for pair in ([s1, s2], [s1, s3]):
+            with pytest.raises(coral.CoralError) as e:
+                coral.Batch(pair)
+            assert e.value.code == coral.E_INVALID
+    finally:
+        for s in (s1, s2, s3):
+            s.close()
