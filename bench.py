@@ -36,6 +36,8 @@ WORKLOADS = {
             "merge+mutation every 20 steps",
     "cfg2": "1024x1024 torus, 64 Voronoi genomes, 54->32->10 CPPN nets, mutation every 50 steps",
     "cfg1": "64x64 torus, 8 Voronoi genomes, direct 54->10 nets",
+    "cfg4": "256 independent square worlds, side log-uniform in [128, 2048], 16-256 Voronoi genomes "
+            "each, 54->32->10 CPPN nets, stepped together (one launch per pass, CUDA graph replay)",
 }
 STATE_BYTES = 29          # E, I, C0..C3 float32 + G int32 + R uint8 per cell
 P1_BYTES = 45             # pass 1 reads the state (29 B) and writes C' (16 B)
@@ -54,6 +56,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batched-steps", type=int, default=10, help="steps of the 256-world batch (0 = skip)")
     return ap.parse_args()
 
 
@@ -219,6 +222,32 @@ def cpu_baseline(workload, seed, budget, rows=16):
                       f"step 0, {d['seconds']:.1f} s, 1 thread (FP64 numpy oracle)"}
 
 
+# ----------------------------------------------------------------------------- batched worlds
+
+def run_batched(n_worlds, steps, warmup, seed, tune=True):
+    """cfg4: many worlds of different sizes stepped as one batch. Returns a dict of figures."""
+    import torch
+
+    from paper_2406_09654_gb300 import coral, worlds
+    ws = worlds.make_batch_worlds(n_worlds, seed=seed)
+    subs = [coral.substrate_for_world(w, coral.BF16_GROUPED) for w in ws]
+    cells = sum(w.n_cells for w in ws)
+    try:
+        with coral.Batch(subs) as b:
+            choice = b.tune(trial_steps=2) if tune else None
+            b.step(warmup)
+            torch.cuda.synchronize()
+            ms = b.step_timed(steps)
+    finally:
+        for s in subs:
+            s.close()
+    total = float(np.sum(ms))
+    return {"value": cells * steps / (total / 1e3), "unit": "cell-updates/s", "worlds": n_worlds, "cells": cells,
+            "steps": steps, "ms_per_step": total / steps, "p50_step_ms": float(np.percentile(ms, 50)),
+            "p99_step_ms": float(np.percentile(ms, 99)), "tuned": choice,
+            "step_hbm_frac": STATE_BYTES * 2 * cells / (total / steps / 1e3) / 1e9 / measured_peaks()[0]}
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_coral(a, rank, world_size, local):
@@ -317,6 +346,9 @@ def run_coral(a, rank, world_size, local):
         e2e = {"value": N * a.e2e_steps * world_size / el, "unit": "cell-updates/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     sub.close()
+    batched = None
+    if path == "bf16" and a.batched_steps > 0:
+        batched = run_batched(256, a.batched_steps, 2, seed=rank)
 
     if rank != 0:
         return None
@@ -341,6 +373,7 @@ def run_coral(a, rank, world_size, local):
         "clocks": {"sm_mhz": ck.get("sm_mhz"), "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons", [])},
         "e2e": e2e,
         "gpu_launches": launches,
+        "batched_cfg4": batched,
     }
     return line
 
@@ -369,6 +402,25 @@ def main():
                                  "sample": "each step: one band of 16 full rows of the world through the FP64 oracle"},
                 "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             }))
+        return
+    if a.workload == "cfg4":
+        import torch
+        torch.cuda.set_device(local)
+        from paper_2406_09654_gb300 import build
+        build.build()
+        barrier(world_size)
+        t0 = time.perf_counter()
+        r = run_batched(256, a.steps, a.warmup, seed=rank)
+        el = max_over_ranks(r["ms_per_step"] * a.steps / 1e3, world_size)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": r["cells"] * a.steps * world_size / el, "unit": "cell-updates/s",
+                              "n_gpus": world_size, "steps": a.steps, "warmup": a.warmup,
+                              "ms_per_step": 1e3 * el / a.steps, "higher_is_better": True, "scaling": "weak",
+                              "vs_baseline": None, "dtype": "bf16 network operands, f32 accumulation and state",
+                              "data": "synthetic", "config": {"workload": f"cfg4: {WORKLOADS['cfg4']}",
+                                                              "cells": r["cells"], "tuned": r["tuned"]},
+                              "p50_step_ms": r["p50_step_ms"], "p99_step_ms": r["p99_step_ms"],
+                              "wall_s": time.perf_counter() - t0}))
         return
     cb = None
     if rank == 0 and world_size == 1 and not a.no_cpu_baseline:

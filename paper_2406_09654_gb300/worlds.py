@@ -230,6 +230,40 @@ def make_world(preset: str | None = None, seed: int = 0, **overrides) -> World:
                  steps=int(cfg.get("steps", 1)), name=preset or "custom")
 
 
+def _block_voronoi(width, height, n, rng, block=8):
+    """Voronoi blobs computed on 8x8-cell blocks (seeds at block centres, torus distance in
+    blocks, ties to the lower seed), then expanded to cells: the layout of large worlds."""
+    bw, bh = -(-width // block), -(-height // block)
+    if n > bw * bh:
+        return _torus_voronoi(width, height, n, rng)
+    Gb = _torus_voronoi(bw, bh, n, rng)
+    return np.repeat(np.repeat(Gb, block, axis=0), block, axis=1)[:height, :width].astype(np.int32)
+
+
+def make_batch_worlds(n_worlds: int = 256, side_min: int = 128, side_max: int = 2048,
+                      genomes=(16, 256), hidden: int = 32, seed: int = 0):
+    """Independent square worlds for batched stepping: side log-uniform in [side_min, side_max],
+    genome count uniform in the given range, CPPN nets 54->hidden->10, no radiation. Channels
+    are drawn in float32 (same distributions as make_world); genomes sit in Voronoi blobs
+    computed on 8x8-cell blocks."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, n_worlds, side_min, side_max, 4]))
+    sides = np.rint(np.exp(rng.uniform(np.log(side_min), np.log(side_max), n_worlds))).astype(int)
+    counts = rng.integers(genomes[0], genomes[1] + 1, n_worlds)
+    out = []
+    for k in range(n_worlds):
+        s, n = int(sides[k]), int(counts[k])
+        r = np.random.default_rng(np.random.SeedSequence([seed, k, s, n]))
+        E = r.random((s, s), dtype=np.float32)
+        I = (0.5 * r.random((s, s), dtype=np.float32)).astype(np.float32)
+        C = (0.1 * r.standard_normal((4, s, s), dtype=np.float32)).astype(np.float32)
+        G = _block_voronoi(s, s, n, r)
+        genes = r.normal(0.0, 1.0, (n, N_GENES)).astype(np.float32)
+        phys = dict(DEFAULT_PHYSICS, radiation_every=0, p_mut=0.0, p_merge=0.0)
+        out.append(World(s, s, E, I, C, G, np.zeros((s, s), np.uint8), n, hidden, n, genes=genes,
+                         physics=phys, seed=seed * 100003 + k, steps=200, name=f"batch{k}"))
+    return out
+
+
 def sample_cells(world: World, n: int, seed: int = 1) -> np.ndarray:
     """Seeded sample of distinct flat cell indices (for per-cell checks at full size)."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, world.n_cells, 7]))
