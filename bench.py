@@ -38,6 +38,9 @@ WORKLOADS = {
     "cfg1": "64x64 torus, 8 Voronoi genomes, direct 54->10 nets",
     "cfg4": "256 independent square worlds, side log-uniform in [128, 2048], 16-256 Voronoi genomes "
             "each, 54->32->10 CPPN nets, stepped together (one launch per pass, CUDA graph replay)",
+    "cfg5": "serving: Poisson arrivals at 200/s of world-stepping requests, side log-uniform in "
+            "[128, 4096], 8-1024 genomes, 10-1000 steps each, 54->32->10 CPPN nets, admitted by a "
+            "150 GB device-memory budget, continuous batching",
 }
 STATE_BYTES = 29          # E, I, C0..C3 float32 + G int32 + R uint8 per cell
 P1_BYTES = 45             # pass 1 reads the state (29 B) and writes C' (16 B)
@@ -57,6 +60,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batched-steps", type=int, default=10, help="steps of the 256-world batch (0 = skip)")
+    ap.add_argument("--serving-requests", type=int, default=16, help="requests of the serving run (0 = skip)")
     return ap.parse_args()
 
 
@@ -248,6 +252,20 @@ def run_batched(n_worlds, steps, warmup, seed, tune=True):
             "step_hbm_frac": STATE_BYTES * 2 * cells / (total / steps / 1e3) / 1e9 / measured_peaks()[0]}
 
 
+# ----------------------------------------------------------------------------- serving
+
+def run_serving(n_requests, seed, budget_gb=150.0, rate=200.0):
+    """cfg5: continuous-batching world server over seeded Poisson requests."""
+    from paper_2406_09654_gb300 import serving, worlds
+    reqs = serving.poisson_requests(n_requests, rate, worlds.request_world_factory((128, 4096), (8, 1024), 32),
+                                    (10, 1000), seed=seed)
+    srv = serving.WorldServer(serving.CoralBackend(), budget_bytes=int(budget_gb * (1 << 30)), chunk_steps=8)
+    _, rep = srv.run(reqs)
+    rep["requests_generated"] = n_requests
+    rep["rate_per_s"] = rate
+    return rep
+
+
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_coral(a, rank, world_size, local):
@@ -346,9 +364,11 @@ def run_coral(a, rank, world_size, local):
         e2e = {"value": N * a.e2e_steps * world_size / el, "unit": "cell-updates/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     sub.close()
-    batched = None
+    batched = served = None
     if path == "bf16" and a.batched_steps > 0:
         batched = run_batched(256, a.batched_steps, 2, seed=rank)
+    if path == "bf16" and a.serving_requests > 0:
+        served = run_serving(a.serving_requests, seed=rank)
 
     if rank != 0:
         return None
@@ -374,6 +394,7 @@ def run_coral(a, rank, world_size, local):
         "e2e": e2e,
         "gpu_launches": launches,
         "batched_cfg4": batched,
+        "serving_cfg5": served,
     }
     return line
 
@@ -402,6 +423,20 @@ def main():
                                  "sample": "each step: one band of 16 full rows of the world through the FP64 oracle"},
                 "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             }))
+        return
+    if a.workload == "cfg5":
+        import torch
+        torch.cuda.set_device(local)
+        from paper_2406_09654_gb300 import build
+        build.build()
+        r = run_serving(a.steps, seed=rank)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": r["cell_updates_per_s"], "unit": "cell-updates/s",
+                              "n_gpus": world_size, "steps": a.steps, "warmup": 0, "higher_is_better": True,
+                              "scaling": "weak", "vs_baseline": None,
+                              "dtype": "bf16 network operands, f32 accumulation and state", "data": "synthetic",
+                              "config": {"workload": f"cfg5: {WORKLOADS['cfg5']}", "requests": a.steps},
+                              "p50_step_ms": r["p50_step_ms"], "p99_step_ms": r["p99_step_ms"], "serving": r}))
         return
     if a.workload == "cfg4":
         import torch

@@ -79,7 +79,7 @@ struct Partial {   // per-block partial sums of one step (FP64), fixed-order com
   long long c[2];  // explore, takeover
 };
 
-struct StepArgs {
+struct __align__(8) StepArgs {
   int W, H;
   long long N;
   int hidden;
@@ -192,6 +192,14 @@ bool encode_sensor_tmap(CUtensorMap* map, const float* E, int W, int H);
 cudaError_t launch_pass2(const StepArgs& a, cudaStream_t st, int grid);
 cudaError_t launch_stats(const StepArgs& a, int n_part1, int n_part2, long long t,
                          coral_stats* ring, cudaStream_t st);
+// Copies one world's step arguments to shared memory (called by every thread of the block,
+// followed by a barrier), so the kernel body reads them with shared loads.
+__device__ __forceinline__ void copy_args_to_shared(StepArgs* dst, const StepArgs* src) {
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(StepArgs) / sizeof(int)); i += blockDim.x) d[i] = s[i];
+}
+
 cudaError_t prepare_pass1_bf16_batch();   // kernel attributes, once before any capture
 cudaError_t launch_pass1_bf16_batch(const BatchTable& b, int parity, int grid, cudaStream_t st);
 cudaError_t launch_pass2_batch(const BatchTable& b, int parity, int grid, cudaStream_t st);

@@ -422,8 +422,11 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm)
 
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16_batch(const __grid_constant__ BatchTable bt,
                                                                           const int parity) {
+  __shared__ StepArgs sa;
   const int w = bt.cta_world1[blockIdx.x];
-  pass1_bf16_body(bt.args[parity * bt.n + w], nullptr, 0, blockIdx.x - bt.world_first1[w], bt.world_ctas1[w]);
+  copy_args_to_shared(&sa, &bt.args[parity * bt.n + w]);
+  __syncthreads();
+  pass1_bf16_body(sa, nullptr, 0, blockIdx.x - bt.world_first1[w], bt.world_ctas1[w]);
 }
 
 }  // namespace

@@ -327,8 +327,10 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2_x4(const __grid_constant__
 }
 
 __global__ void __launch_bounds__(kP2Threads) k_pass2_batch(const __grid_constant__ BatchTable bt, const int parity) {
+  __shared__ StepArgs a;
   const int w = bt.cta_world2[blockIdx.x];
-  const StepArgs& a = bt.args[parity * bt.n + w];
+  copy_args_to_shared(&a, &bt.args[parity * bt.n + w]);
+  __syncthreads();
   const int cta = blockIdx.x - bt.world_first2[w], ncta = bt.world_ctas2[w];
   if ((a.W & 3) == 0 && a.W >= 8)
     pass2_x4_body(a, cta, ncta);

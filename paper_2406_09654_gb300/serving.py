@@ -1,0 +1,183 @@
+"""Continuous-batching server for world-stepping requests.
+
+A request asks for one world (its seeded state and genome table) to be stepped a given number
+of times. Requests arrive over time; the server admits them in arrival order as soon as the
+memory they need fits in the budget, keeps every admitted world resident on the device, and
+steps all resident worlds together: one batched launch per pass over every world (the
+library's coral_batch_*), so a request that arrives while others run joins the next step and
+its work overlaps theirs on the device. A world that has done its steps is read back and freed,
+which may admit waiting requests. Because the batched kernels run the same per-cell arithmetic
+as single-world stepping, each result is identical to stepping the world alone.
+
+The device side is behind a small backend interface (``CoralBackend``) so that the scheduling
+logic can be exercised on the CPU with a fake backend.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# Device bytes per cell of a resident world: two state buffers (2 x 29 B), the pass-1 record
+# and direction (17 B); plus per genome slot the FP32 and BF16 nets and genes (~8.6 KB at
+# H = 32) and a fixed part (stats ring, partial sums, radiation scratch).
+BYTES_PER_CELL = 2 * 29 + 17
+BYTES_PER_SLOT = {0: 2400 + 2200, 16: 4200 + 2600, 32: 6600 + 4200, 48: 8900 + 6300, 64: 17300 + 10400}
+FIXED_BYTES = 2 << 20
+
+
+def world_bytes(n_cells: int, capacity: int, hidden: int) -> int:
+    return n_cells * BYTES_PER_CELL + capacity * BYTES_PER_SLOT.get(hidden, 20000) + FIXED_BYTES
+
+
+@dataclass(order=True)
+class Request:
+    arrival: float                      # seconds after the start of the run
+    rid: int
+    world: object = field(compare=False)
+    steps: int = field(compare=False, default=1)
+
+
+@dataclass
+class Completed:
+    rid: int
+    arrival: float
+    admitted: float
+    finished: float
+    steps: int
+    cells: int
+    result: dict                        # the world's channels after its last step
+
+
+class CoralBackend:
+    """Real device backend: substrates and batches of the CUDA library."""
+
+    def __init__(self, path=None):
+        from . import coral
+        self.coral = coral
+        self.path = coral.BF16_GROUPED if path is None else path
+
+    def create(self, world):
+        return self.coral.substrate_for_world(world, self.path)
+
+    def batch(self, handles):
+        return self.coral.Batch(handles)
+
+    def step(self, batch, n):
+        return batch.step_timed(n)       # per-step device time (ms)
+
+    def read(self, handle):
+        return handle.read_channels()
+
+    def free(self, handle):
+        handle.close()
+
+    def free_batch(self, batch):
+        batch.close()
+
+
+class WorldServer:
+    """Admits requests by memory budget and steps the resident worlds as one batch."""
+
+    def __init__(self, backend, budget_bytes: int, chunk_steps: int = 4, clock=time.perf_counter,
+                 sleep=time.sleep):
+        self.backend = backend
+        self.budget = int(budget_bytes)
+        self.chunk = max(1, int(chunk_steps))
+        self.clock = clock
+        self.sleep = sleep
+
+    def run(self, requests):
+        """Serve `requests` (arrival times in seconds from now). Returns (completed, report)."""
+        pending = sorted(requests)
+        waiting = []                     # arrived, not admitted (FIFO by arrival)
+        active = {}                      # rid -> [request, handle, remaining, admitted_at, bytes]
+        used = 0
+        batch = None
+        dirty = False
+        step_lat = []                    # (batch step ms, resident worlds) per batched step
+        req_step_ms = []                 # one entry per request-step: the step time it saw
+        completed = []
+        work = 0
+        t0 = self.clock()
+        peak_used = 0
+        while pending or waiting or active:
+            now = self.clock() - t0
+            while pending and pending[0].arrival <= now:
+                waiting.append(pending.pop(0))
+            # admission: arrival order, while the budget allows (a request that can never fit
+            # on its own is rejected rather than blocking the queue)
+            while waiting:
+                r = waiting[0]
+                need = world_bytes(r.world.n_cells, r.world.capacity, r.world.hidden)
+                if need > self.budget:
+                    waiting.pop(0)
+                    completed.append(Completed(r.rid, r.arrival, -1.0, -1.0, 0, r.world.n_cells, {}))
+                    continue
+                if used + need > self.budget:
+                    break
+                waiting.pop(0)
+                active[r.rid] = [r, self.backend.create(r.world), r.steps, self.clock() - t0, need]
+                used += need
+                peak_used = max(peak_used, used)
+                dirty = True
+            if not active:
+                if pending:                                   # idle until the next arrival
+                    self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
+                continue
+            if dirty or batch is None:
+                if batch is not None:
+                    self.backend.free_batch(batch)
+                batch = self.backend.batch([v[1] for v in active.values()])
+                dirty = False
+            n = min(self.chunk, min(v[2] for v in active.values()))
+            ms = self.backend.step(batch, n)
+            for m in ms:
+                step_lat.append((float(m), len(active)))
+                req_step_ms.extend([float(m)] * len(active))
+            work += n * sum(v[0].world.n_cells for v in active.values())
+            done = [rid for rid, v in active.items() if v[2] - n <= 0]
+            for v in active.values():
+                v[2] -= n
+            if done:
+                self.backend.free_batch(batch)
+                batch = None
+                for rid in done:
+                    r, h, _, adm, need = active.pop(rid)
+                    res = self.backend.read(h)
+                    self.backend.free(h)
+                    used -= need
+                    completed.append(Completed(rid, r.arrival, adm, self.clock() - t0, r.steps,
+                                               r.world.n_cells, res))
+        if batch is not None:
+            self.backend.free_batch(batch)
+        makespan = self.clock() - t0
+        lat = np.array(req_step_ms) if req_step_ms else np.zeros(1)
+        served = [c for c in completed if c.admitted >= 0]
+        report = {
+            "requests": len(completed), "served": len(served),
+            "rejected": len(completed) - len(served),
+            "makespan_s": makespan, "cell_updates": work,
+            "cell_updates_per_s": work / makespan if makespan > 0 else 0.0,
+            "p50_step_ms": float(np.percentile(lat, 50)), "p99_step_ms": float(np.percentile(lat, 99)),
+            "batched_steps": len(step_lat),
+            "mean_resident_worlds": float(np.mean([k for _, k in step_lat])) if step_lat else 0.0,
+            "p50_queue_s": float(np.percentile([c.admitted - c.arrival for c in served], 50)) if served else 0.0,
+            "p99_queue_s": float(np.percentile([c.admitted - c.arrival for c in served], 99)) if served else 0.0,
+            "peak_resident_bytes": peak_used, "budget_bytes": self.budget,
+        }
+        return completed, report
+
+
+def poisson_requests(n: int, rate: float, make_world, steps_range=(10, 1000), seed: int = 0):
+    """n requests with exponential inter-arrival times (rate per second); make_world(rng, k)
+    builds request k's world; steps uniform in steps_range."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, n, 5]))
+    t = 0.0
+    out = []
+    for k in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        steps = int(rng.integers(steps_range[0], steps_range[1] + 1))
+        out.append(Request(t, k, make_world(rng, k), steps))
+    return out

@@ -249,19 +249,33 @@ def make_batch_worlds(n_worlds: int = 256, side_min: int = 128, side_max: int = 
     rng = np.random.default_rng(np.random.SeedSequence([seed, n_worlds, side_min, side_max, 4]))
     sides = np.rint(np.exp(rng.uniform(np.log(side_min), np.log(side_max), n_worlds))).astype(int)
     counts = rng.integers(genomes[0], genomes[1] + 1, n_worlds)
-    out = []
-    for k in range(n_worlds):
-        s, n = int(sides[k]), int(counts[k])
-        r = np.random.default_rng(np.random.SeedSequence([seed, k, s, n]))
-        E = r.random((s, s), dtype=np.float32)
-        I = (0.5 * r.random((s, s), dtype=np.float32)).astype(np.float32)
-        C = (0.1 * r.standard_normal((4, s, s), dtype=np.float32)).astype(np.float32)
-        G = _block_voronoi(s, s, n, r)
-        genes = r.normal(0.0, 1.0, (n, N_GENES)).astype(np.float32)
-        phys = dict(DEFAULT_PHYSICS, radiation_every=0, p_mut=0.0, p_merge=0.0)
-        out.append(World(s, s, E, I, C, G, np.zeros((s, s), np.uint8), n, hidden, n, genes=genes,
-                         physics=phys, seed=seed * 100003 + k, steps=200, name=f"batch{k}"))
-    return out
+    return [make_square_world(int(sides[k]), int(counts[k]), hidden, seed * 100003 + k, f"batch{k}")
+            for k in range(n_worlds)]
+
+
+def make_square_world(side: int, n_genomes: int, hidden: int = 32, seed: int = 0, name: str = "") -> World:
+    """One side x side world with n_genomes CPPN genomes in block-Voronoi blobs, no radiation;
+    channels drawn in float32 with make_world's distributions."""
+    s, n = int(side), int(n_genomes)
+    r = np.random.default_rng(np.random.SeedSequence([seed, s, n, hidden, 6]))
+    E = r.random((s, s), dtype=np.float32)
+    I = (0.5 * r.random((s, s), dtype=np.float32)).astype(np.float32)
+    C = (0.1 * r.standard_normal((4, s, s), dtype=np.float32)).astype(np.float32)
+    G = _block_voronoi(s, s, min(n, s * s), r)
+    genes = r.normal(0.0, 1.0, (n, N_GENES)).astype(np.float32)
+    phys = dict(DEFAULT_PHYSICS, radiation_every=0, p_mut=0.0, p_merge=0.0)
+    return World(s, s, E, I, C, G, np.zeros((s, s), np.uint8), n, hidden, n, genes=genes,
+                 physics=phys, seed=seed, steps=1, name=name or f"square{s}")
+
+
+def request_world_factory(side_range=(128, 4096), genomes_range=(8, 1024), hidden: int = 32):
+    """make_world(rng, k) for serving requests: side log-uniform in side_range, genome count
+    uniform in genomes_range (capped by the cell count)."""
+    def make(rng, k):
+        side = int(np.rint(np.exp(rng.uniform(np.log(side_range[0]), np.log(side_range[1])))))
+        n = int(rng.integers(genomes_range[0], genomes_range[1] + 1))
+        return make_square_world(side, min(n, side * side), hidden, seed=int(rng.integers(1 << 30)), name=f"req{k}")
+    return make
 
 
 def sample_cells(world: World, n: int, seed: int = 1) -> np.ndarray:
