@@ -197,33 +197,42 @@ st = O.State.from_world(w)
 p = O.Params.from_world(w)
 nets = O.nets_from_genomes(O.Genomes.from_genes(w.genes, w.n_genomes), w.hidden) if w.genes is not None \
     else O.Nets.from_dense(w.dense, w.hidden)
-rows = {rows}
-budget = {budget}
-done = 0; spent = 0.0; bands = 0
+rows, budget, max_bands = {rows}, {budget}, {max_bands}
+times, cells = [], []
 y = 0
-while (spent < budget or bands == 0) and y < w.height:
-    cells = np.arange(y * w.width, min(w.height, y + rows) * w.width)
+while len(times) < max_bands and (sum(times) < budget or len(times) < {min_bands}):
+    band = np.arange(y * w.width, min(w.height, y + rows) * w.width)
     t0 = time.perf_counter()
-    O.step_cells(st, nets, 0, p, cells)
-    spent += time.perf_counter() - t0
-    done += len(cells); bands += 1; y += rows
-print(json.dumps(dict(cells=done, seconds=spent, bands=bands)))
+    O.step_cells(st, nets, 0, p, band)
+    times.append(time.perf_counter() - t0)
+    cells.append(len(band))
+    y = (y + rows) % w.height
+print(json.dumps(dict(times=times, cells=cells)))
 """
 
 
-def cpu_baseline(workload, seed, budget, rows=16):
-    """The FP64 oracle as it stands, one thread, on bands of `rows` full rows of the same world
-    (pass 1 on the band and its neighbours, pass 2 on the band) until about `budget` seconds."""
+def oracle_bands(workload, seed, budget, min_bands=1, max_bands=10**6, rows=16):
+    """Runs the FP64 oracle as it stands, one thread, on successive bands of `rows` full rows of
+    the same world (pass 1 on the band and its neighbours, pass 2 on the band) until about
+    `budget` seconds, in a fresh process; returns per-band (seconds, cells)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = CPU_SNIPPET.format(root=ROOT, workload=workload, seed=seed, rows=rows, budget=budget)
+    code = CPU_SNIPPET.format(root=ROOT, workload=workload, seed=seed, rows=rows, budget=budget,
+                              min_bands=min_bands, max_bands=max_bands)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
-        return {"value": None, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                "sample": "failed: " + r.stderr[-300:]}
+        raise RuntimeError(r.stderr[-400:])
     d = json.loads(r.stdout.strip().splitlines()[-1])
-    return {"value": d["cells"] / d["seconds"], "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{d['bands']} bands of {rows} full rows ({d['cells']} cells) of the same world, "
-                      f"step 0, {d['seconds']:.1f} s, 1 thread (FP64 numpy oracle)"}
+    return d["times"], d["cells"]
+
+
+def cpu_baseline(workload, seed, budget, rows=16):
+    try:
+        times, cells = oracle_bands(workload, seed, budget, rows=rows)
+    except RuntimeError as e:
+        return {"value": None, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+    return {"value": sum(cells) / sum(times), "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(times)} bands of {rows} full rows ({sum(cells)} cells) of the same world, "
+                      f"step 0, {sum(times):.1f} s, 1 thread (FP64 numpy oracle)"}
 
 
 # ----------------------------------------------------------------------------- batched worlds
@@ -404,23 +413,19 @@ def main():
     rank, world_size, local = dist_setup(a.gpus)
     if a.impl == "reference":
         if rank == 0:
-            per = []
-            cb = None
-            for k in range(a.warmup + a.steps):
-                cb = cpu_baseline(a.workload, 0, 0.0)
-                if k >= a.warmup:
-                    per.append(cb)
-            cells = sum(int(c["sample"].split("(")[1].split()[0]) for c in per)
-            secs = sum(int(c["sample"].split("(")[1].split()[0]) / c["value"] for c in per)
-            v = cells / secs
+            wl = a.workload if a.workload in ("cfg1", "cfg2", "cfg3") else "cfg3"
+            times, cells = oracle_bands(wl, 0, 0.0, min_bands=a.warmup + a.steps, max_bands=a.warmup + a.steps)
+            t, c = times[a.warmup:], cells[a.warmup:]
+            v = sum(c) / sum(t)
+            sample = (f"each step: one band of 16 full rows ({c[0]} cells) of the {wl} world through the FP64 "
+                      f"numpy oracle, 1 thread")
             print(json.dumps({
                 "impl": "reference", "metric": METRIC, "value": v, "unit": "cell-updates/s",
                 "n_gpus": world_size, "steps": a.steps, "warmup": a.warmup,
-                "ms_per_step": 1e3 * secs / len(per), "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"{a.workload}: {WORKLOADS[a.workload]}", "path": "oracle"},
-                "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-                                 "sample": "each step: one band of 16 full rows of the world through the FP64 oracle"},
+                "config": {"workload": f"{wl}: {WORKLOADS[wl]}", "path": "oracle"},
+                "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
                 "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             }))
         return
