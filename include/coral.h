@@ -197,6 +197,16 @@ int coral_read_genomes(coral_substrate* s, float* genes, int32_t* parent);
 /* Reads slot's FP32 dense net in the dense_or_null layout of coral_genome_table_load. */
 int coral_read_weights(coral_substrate* s, int32_t slot, float* dst, size_t dst_floats);
 
+/*
+ * Genetic similarity (Section "Discussion and Future Work": NEAT's measure of genetic
+ * similarity). NEAT's compatibility distance is c1 E/N + c2 D/N + c3 W, W the mean weight
+ * difference of matching genes; the CPPNs here share one topology (no excess or disjoint
+ * genes), so the distance is c3 * mean_k |g_a[k] - g_b[k]| over the 18 genes, c3 = 0.4.
+ * slots: host int32 [n] genome slots; out: host float32 [n][n]. n in [1, 4096]. Synchronises.
+ * Phylogeny: the parent column of coral_read_genomes links every born genome to its parent.
+ */
+int coral_genome_distances(coral_substrate* s, const int32_t* slots, int32_t n, float* out);
+
 /* Step index of the next coral_step (for checkpoint/resume; Philox is keyed by it). */
 int coral_set_step(coral_substrate* s, int64_t t);
 int coral_get_step(const coral_substrate* s, int64_t* t);

@@ -570,6 +570,36 @@ def radiation(st: State, gen: Genomes, t: int, p: Params):
     return new_st, new_gen, slots, ev
 
 
+# --------------------------------------------------------------------------------------
+# genetic similarity and phylogeny (Section "Discussion and Future Work": NEAT's measure of
+# genetic similarity; phylogeny tracking)
+# --------------------------------------------------------------------------------------
+
+NEAT_C3 = 0.4      # weight-difference coefficient of NEAT's compatibility distance
+
+
+def genetic_distance(ga, gb, c3: float = NEAT_C3):
+    """NEAT compatibility distance delta = c1 E/N + c2 D/N + c3 mean|w_a - w_b|; the CPPNs here
+    share one topology, so there are no excess (E) or disjoint (D) genes and delta reduces to
+    c3 times the mean absolute difference of the matching genes."""
+    a = np.asarray(ga, np.float64)
+    b = np.asarray(gb, np.float64)
+    return c3 * float(np.mean(np.abs(a - b)))
+
+
+def lineage(parent, slot):
+    """Ancestors of a genome slot from the parent column (newest first), ending at a loaded
+    genome (parent -1)."""
+    out = []
+    s = int(slot)
+    seen = set()
+    while s >= 0 and s not in seen:
+        seen.add(s)
+        out.append(s)
+        s = int(parent[s])
+    return out
+
+
 def run(st: State, nets: Nets, gen: Genomes | None, t0: int, n_steps: int, p: Params,
         on_step=None):
     """n_steps full steps starting at step index t0, radiation and regeneration included."""

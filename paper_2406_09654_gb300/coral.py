@@ -72,6 +72,7 @@ SIGNATURES = {
     "coral_read_perm": (ctypes.c_int, [_VP, _VP, _VP]),
     "coral_read_genomes": (ctypes.c_int, [_VP, _VP, _VP]),
     "coral_read_weights": (ctypes.c_int, [_VP, _I32, _VP, _SZ]),
+    "coral_genome_distances": (ctypes.c_int, [_VP, _VP, _I32, _VP]),
     "coral_set_step": (ctypes.c_int, [_VP, _I64]),
     "coral_get_step": (ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
     "coral_sync": (ctypes.c_int, [_VP]),
@@ -297,6 +298,13 @@ class Substrate:
         parent = np.empty(self.capacity, np.int32)
         _check(lib().coral_read_genomes(self.h, genes.ctypes.data, parent.ctypes.data), self.h)
         return genes, parent
+
+    def genome_distances(self, slots):
+        """NEAT compatibility distances [n][n] between the listed genome slots."""
+        sl = np.ascontiguousarray(slots, np.int32)
+        out = np.empty((len(sl), len(sl)), np.float32)
+        _check(lib().coral_genome_distances(self.h, sl.ctypes.data, len(sl), out.ctypes.data), self.h)
+        return out
 
     def read_weights(self, slot):
         nf = lib().coral_net_floats(self.params.hidden)

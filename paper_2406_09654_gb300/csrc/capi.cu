@@ -512,6 +512,24 @@ int coral_read_weights(coral_substrate* s, int32_t slot, float* dst, size_t dst_
   return check_status(s);
 }
 
+int coral_genome_distances(coral_substrate* s, const int32_t* slots, int32_t n, float* out) {
+  if (!s || !slots || !out) return fail(s, CORAL_E_INVALID, "NULL argument");
+  if (n < 1 || n > 4096) return fail(s, CORAL_E_INVALID, "n must be in [1, 4096]");
+  for (int i = 0; i < n; ++i)
+    if (slots[i] < 0 || slots[i] >= s->cap) return fail(s, CORAL_E_INVALID, "slot out of range");
+  const size_t pairs = (size_t)n * n;
+  void* tmp = nullptr;
+  CK(s, cudaMallocAsync(&tmp, sizeof(int32_t) * n + sizeof(float) * pairs + 256, s->stream));
+  int32_t* dslots = static_cast<int32_t*>(tmp);
+  float* dout = reinterpret_cast<float*>(static_cast<char*>(tmp) + ((sizeof(int32_t) * n + 255) & ~(size_t)255));
+  cudaError_t e = cudaMemcpyAsync(dslots, slots, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = launch_genome_distances(s->g.genes, dslots, n, dout, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out, dout, sizeof(float) * pairs, cudaMemcpyDeviceToHost, s->stream);
+  cudaFreeAsync(tmp, s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "genome distances");
+  return check_status(s);
+}
+
 int coral_set_step(coral_substrate* s, int64_t t) {
   if (!s || t < 0) return fail(s, CORAL_E_INVALID, "bad argument");
   s->t = t;

@@ -446,7 +446,26 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const int32_t* ki
   }
 }
 
+// NEAT compatibility distance of fixed-topology genomes: 0.4 * mean |g_a - g_b| (18 genes).
+__global__ void k_genome_distances(const float* genes, const int32_t* slots, int n, float* out) {
+  const long long pair = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pair >= (long long)n * n) return;
+  const int i = (int)(pair / n), k = (int)(pair - (long long)i * n);
+  const float* a = genes + (long long)slots[i] * kGenes;
+  const float* b = genes + (long long)slots[k] * kGenes;
+  float acc = 0.0f;
+#pragma unroll
+  for (int g = 0; g < kGenes; ++g) acc += fabsf(a[g] - b[g]);
+  out[pair] = 0.4f * (acc / (float)kGenes);
+}
+
 }  // namespace
+
+cudaError_t launch_genome_distances(const float* genes, const int32_t* slots, int n, float* out, cudaStream_t st) {
+  const long long pairs = (long long)n * n;
+  k_genome_distances<<<(int)((pairs + 255) / 256), 256, 0, st>>>(genes, slots, n, out);
+  return cudaGetLastError();
+}
 
 int radiation_blocks(long long N) { return (int)((N + kRadTile - 1) / kRadTile); }
 int bucket_blocks(long long N) { return (int)((N + kSortTile - 1) / kSortTile); }

@@ -255,3 +255,20 @@ def test_errors_are_reported():
         assert e.value.code == coral.E_INVALID
         sub.load_state(G=w.G)
         sub.sync()
+
+
+def test_genome_distances_and_lineage_after_radiation():
+    w = worlds.make_world(width=96, height=64, n_genomes=10, hidden=16, net="cppn", seed=21,
+                          radiation_every=1, p_mut=4e-3, p_merge=8e-3, capacity=200)
+    with coral.substrate_for_world(w, coral.FP32_PERCELL) as sub:
+        sub.step(3)
+        genes, parent = sub.read_genomes()
+        born = [s for s in range(200) if parent[s] >= 0]
+        slots = np.array(list(range(10)) + born[:20], np.int32)
+        d = sub.genome_distances(slots)
+    for i, a in enumerate(slots):
+        for k, b in enumerate(slots):
+            assert d[i, k] == pytest.approx(O.genetic_distance(genes[a], genes[b]), rel=1e-5, abs=1e-7)
+    for s in born:
+        anc = O.lineage(parent, s)
+        assert anc[0] == s and parent[anc[-1]] == -1 and anc[-1] < 10

@@ -555,3 +555,22 @@ def test_explore_argmax_on_preactivations_breaks_saturated_ties():
     d, amt, margin = O.explore_decision(z, a, np.array([1.0]), np.array([0]), O.Params())
     assert d[0] == 3 and margin[0] == pytest.approx(1.0)          # logit k=2 -> left of north
     assert amt[0] == pytest.approx(0.5 * math.tanh(13.0))
+
+
+# ----------------------------------------------------------------------------- genetic distance
+
+def test_genetic_distance_closed_forms():
+    g = np.random.default_rng(0).normal(size=18)
+    assert O.genetic_distance(g, g) == 0.0
+    h = g.copy(); h[5] += 0.9
+    assert O.genetic_distance(g, h) == pytest.approx(0.4 * 0.9 / 18, abs=1e-15)
+    k = np.random.default_rng(1).normal(size=18)
+    assert O.genetic_distance(g, k) == pytest.approx(O.genetic_distance(k, g), abs=0)
+    m = np.random.default_rng(2).normal(size=18)
+    assert O.genetic_distance(g, m) <= O.genetic_distance(g, k) + O.genetic_distance(k, m) + 1e-15
+
+
+def test_lineage_follows_parents():
+    parent = np.array([-1, -1, 0, 2, 1, 3])
+    assert O.lineage(parent, 5) == [5, 3, 2, 0]
+    assert O.lineage(parent, 4) == [4, 1]
