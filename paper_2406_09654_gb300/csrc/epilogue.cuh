@@ -15,12 +15,13 @@ struct CellOut {
 // a[0..3] com, a[4] invest, a[5] liquidate, a[6..9] explore (fwd, right, left, back);
 // z[6..9]: pre-activations of the explore actuators (tanh is strictly increasing, so the
 // maximal actuator and its sign are read off z, where saturated outputs cannot tie).
-// E, I: the cell's state; S: FP64 sum of I_t over its 4 von Neumann neighbours; r: rotation.
+// E, I: the cell's state; Sf: the sum of I_t over its 4 von Neumann neighbours, summed in FP64
+// and rounded once to float32 (Sf > 0 exactly when the sum is > 0); r: rotation.
 // kFast: hardware exp / reciprocal / reciprocal-square-root approximations (relative error
 // ~1e-6, far inside the BF16 path's tolerance); otherwise the accurate library functions.
 template <bool kFast = false>
 __device__ __forceinline__ void actuator_epilogue(const StepArgs& p, const float* a, const float* z,
-                                                  float E, float I, double S, int r, CellOut& o) {
+                                                  float E, float I, float Sf, int r, CellOut& o) {
   // Communication: normalised by max(1, ||a0..3||) and passed through a sigmoid.
   const float n2 = a[0] * a[0] + a[1] * a[1] + a[2] * a[2] + a[3] * a[3];
   if (kFast) {
@@ -54,7 +55,6 @@ __device__ __forceinline__ void actuator_epilogue(const StepArgs& p, const float
   o.I1 = I1;
   // Energy flow along infrastructure: the cell keeps (1 - k_flow) E1 when it has somewhere
   // to send, and each neighbour j receives I_t(j) * q with q = k_flow E1 / S.
-  const float Sf = (float)S;          // S >= 0 is a sum of floats: Sf > 0 exactly when S > 0
   const bool send = Sf > 0.0f;
   o.keep = send ? E1 - p.k_flow * E1 : E1;
   o.q = send ? (kFast ? __fdividef(p.k_flow * E1, Sf) : (p.k_flow * E1) / Sf) : 0.0f;

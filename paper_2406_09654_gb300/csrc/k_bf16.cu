@@ -222,10 +222,14 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
                  tc::pack_bf16x2(s[2 * kStageCh], s[3 * kStageCh]),
                  tc::pack_bf16x2(s[4 * kStageCh], s[5 * kStageCh]), 0u);
     }
-    __syncthreads();
+    bool done = g < 0;
+    {
+      const unsigned b = __ballot_sync(0xffffffffu, !done);   // first round's pending rows
+      if (lane == 0) ballots[warp] = b;
+    }
+    __syncthreads();                                  // records and the first ballots visible
     const int hc = (warp + 1) * kHaloW + (lane + 1);
     const uint32_t row_s = a_s + tid * 128;
-    bool done = g < 0;
     float act[kOut], zo[kOut];
 #pragma unroll
     for (int o = 0; o < kOut; ++o) act[o] = zo[o] = 0.0f;
@@ -234,9 +238,11 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     // hidden values), so the input tile is built once per tile
     bool first_round = true;
     while (true) {
-      const unsigned b = __ballot_sync(0xffffffffu, !done);
-      if (lane == 0) ballots[warp] = b;
-      __syncthreads();
+      if (!first_round) {
+        const unsigned b = __ballot_sync(0xffffffffu, !done);
+        if (lane == 0) ballots[warp] = b;
+        __syncthreads();
+      }
       int first = -1;
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
@@ -362,7 +368,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       const int sc = (warp + 1) * kStageW + lane + 4;  // this cell in the stage layout
       const float* sI = stage + kStageCh;
       const double S = (double)sI[sc - kStageW] + (double)sI[sc + 1] + (double)sI[sc + kStageW] + (double)sI[sc - 1];
-      actuator_epilogue<true>(a, act, zo, stage[sc], sI[sc], S, r, o);
+      actuator_epilogue<true>(a, act, zo, stage[sc], sI[sc], (float)S, r, o);
       store_pass1(a, j, o);
     }
     if (valid) {

@@ -138,7 +138,7 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1_fp32(const StepArgs a) {
       }
       // FP64 flow denominator: I_t of the von Neumann neighbours (kernel ranks 1, 4, 5, 8).
       const double S = (double)in[7] + (double)in[25] + (double)in[31] + (double)in[49];
-      actuator_epilogue(a, act, zo, in[0], in[1], S, r, o);
+      actuator_epilogue(a, act, zo, in[0], in[1], (float)S, r, o);
       store_pass1(a, j, o);
     }
 #pragma unroll
