@@ -243,6 +243,16 @@ int coral_batch_step_timed(coral_batch* b, int32_t n_steps, float* step_ms);
  */
 int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* choice);
 
+/*
+ * Failure-detection self-test (library infrastructure; the paper has no counterpart): launches
+ * one CTA that allocates tensor memory and waits, with the same bounded wait the tensor-core
+ * kernel uses, on an mbarrier that nothing arrives on, for about wait_us microseconds of SM
+ * clock (1 .. 1,000,000). The wait runs out, the kernel records CORAL_E_TIMEOUT, frees its
+ * tensor memory and returns; *status_out receives the recorded status. Nothing faults or hangs
+ * and the context stays usable. cuda_stream: NULL = legacy default stream. Synchronises.
+ */
+int coral_selftest_wait_timeout(void* cuda_stream, int32_t wait_us, int32_t* status_out);
+
 /* Waits for the stream and returns the first latched device-side error, if any. */
 int coral_sync(coral_substrate* s);
 

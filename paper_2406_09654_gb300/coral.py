@@ -77,6 +77,7 @@ SIGNATURES = {
     "coral_get_step": (ctypes.c_int, [_VP, ctypes.POINTER(_I64)]),
     "coral_sync": (ctypes.c_int, [_VP]),
     "coral_launch_config": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "coral_selftest_wait_timeout": (ctypes.c_int, [_VP, _I32, _VP]),
     "coral_last_error": (ctypes.c_char_p, [_VP]),
     "coral_net_floats": (_I32, [_I32]),
     "coral_bucket_noalloc": (ctypes.c_int, [_VP, _I64, _I32, _VP, _VP, _VP]),
@@ -402,3 +403,12 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def selftest_wait_timeout(wait_us=1000, stream=None):
+    """Runs the failure-detection self-test; returns the status the kernel recorded
+    (E_TIMEOUT when the bounded wait ran out as designed)."""
+    st = ctypes.c_int32(0)
+    sp = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().coral_selftest_wait_timeout(sp, int(wait_us), ctypes.byref(st)))
+    return st.value

@@ -550,6 +550,28 @@ int coral_launch_config(const coral_substrate* s, int32_t* g1, int32_t* g2, int3
   return CORAL_OK;
 }
 
+int coral_selftest_wait_timeout(void* cuda_stream, int32_t wait_us, int32_t* status_out) {
+  if (!status_out || wait_us < 1 || wait_us > 1000000) return fail(nullptr, CORAL_E_INVALID, "bad arguments");
+  int dev = 0, major = 0, khz = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return fail(nullptr, CORAL_E_CUDA, "cudaGetDevice failed");
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (major != 10) return fail(nullptr, CORAL_E_INVALID, "needs an sm_100-family GPU (tensor memory)");
+  cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev);
+  if (khz <= 0) khz = 2000000;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  int* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemsetAsync(d, 0, sizeof(int), st);
+  if (e == cudaSuccess) e = launch_selftest_wait((long long)khz * 1000LL / 1000000LL * wait_us, d, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  int v = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&v, d, sizeof(int), cudaMemcpyDeviceToHost);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) return fail(nullptr, CORAL_E_CUDA, cudaGetErrorString(e));
+  *status_out = v;
+  return CORAL_OK;
+}
+
 int coral_sync(coral_substrate* s) {
   if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
   return check_status(s);

@@ -205,6 +205,7 @@ cudaError_t launch_pass1_bf16_batch(const BatchTable& b, int parity, int grid, c
 cudaError_t launch_pass2_batch(const BatchTable& b, int parity, int grid, cudaStream_t st);
 cudaError_t launch_stats_batch(const BatchTable& b, cudaStream_t st);
 int pass1_fp32_grid(int sms);
+cudaError_t launch_selftest_wait(long long max_cycles, int* status, cudaStream_t st);
 int pass1_bf16_grid(int sms);
 int pass2_grid(int sms);
 size_t pass1_bf16_smem();

@@ -435,7 +435,40 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16_batch(const
   pass1_bf16_body(sa, nullptr, 0, blockIdx.x - bt.world_first1[w], bt.world_ctas1[w]);
 }
 
+// A wait that must run out: nothing arrives on the barrier. Same bounded wait, error report
+// and TMEM release as the tensor-core kernel's timeout path.
+__global__ void __launch_bounds__(128) k_selftest_wait(long long max_cycles, int* status) {
+  __shared__ uint64_t bar;
+  __shared__ uint32_t slot;
+  const int warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    tc::tmem_alloc(&slot, 32);
+    tc::tmem_relinquish();
+  }
+  if (threadIdx.x == 0) {
+    tc::mbar_init(&bar, 1);
+    tc::fence_barrier_init();
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  bool ok = true;
+  if (threadIdx.x == 0) ok = tc::mbar_wait(&bar, 0, max_cycles);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicCAS(status, 0, (int)CORAL_E_TIMEOUT);
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(slot, 32);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_selftest_wait(long long max_cycles, int* status, cudaStream_t st) {
+  k_selftest_wait<<<1, 128, 0, st>>>(max_cycles, status);
+  return cudaGetLastError();
+}
 
 size_t pass1_bf16_smem() { return kSmemBytes; }
 

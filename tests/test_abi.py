@@ -67,3 +67,11 @@ def test_thresholds():
     from paper_2406_09654_gb300 import coral
     assert coral.threshold(0) == 0 and coral.threshold(1.0) == 0xFFFFFFFF
     assert coral.threshold(1e-4) == 429496
+
+
+def test_selftest_rejects_bad_arguments(lib):
+    from paper_2406_09654_gb300 import coral
+    import ctypes
+    st = ctypes.c_int32(0)
+    assert lib.coral_selftest_wait_timeout(None, 0, ctypes.byref(st)) == coral.E_INVALID
+    assert lib.coral_selftest_wait_timeout(None, 10, None) == coral.E_INVALID
