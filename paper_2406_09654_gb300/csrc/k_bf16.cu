@@ -1,13 +1,16 @@
 // BF16 tensor-core network (pass 1) on tcgen05: each CTA takes a contiguous run of 32x4-cell
-// tiles of the torus, prefetches the next tile's one-cell halo of the six sensor channels into
-// shared memory with cp.async while it works on the current one, builds the
-// 128 x 64 BF16 input tile (the rotation-ordered 3x3 neighbourhood of every cell, K index
-// 6*rank + channel, a constant 1 at K = 54 that carries the layer-1 bias), and runs the genome
-// nets on the tensor cores with FP32 accumulation in TMEM: one 128 x H x 64 MMA for layer 1,
-// tanh in the epilogue (the hidden tile overwrites the consumed input tile, layer 2 reuses the
-// TMEM columns), one 128 x 16 x H MMA for layer 2. A tile with several genomes runs one round per
-// genome (the rows of other genomes are computed and discarded). The actuator
-// epilogue (communication, invest/liquidate, exploration, flow quotient) follows in registers.
+// tiles of the torus. A tile's one-cell halo of the six sensor channels comes into shared memory
+// by one TMA box copy (cp.async where the halo wraps around the torus); the CTA turns it into
+// BF16 cell records and takes each cell's own E, I and flow denominator from it, after which the
+// buffer is free and the next tile's copy overlaps this tile's network. From the records it
+// builds the 128 x 64 BF16 input tile (the rotation-ordered 3x3 neighbourhood of every cell, K
+// index 6*rank + channel, a constant 1 at K = 54 that carries the layer-1 bias) and runs the
+// genome nets on the tensor cores with FP32 accumulation in TMEM: one 128 x H x 64 MMA for
+// layer 1, tanh in the epilogue (the hidden tile overwrites the consumed input tile, layer 2
+// reuses the TMEM columns), one 128 x 16 x H MMA for layer 2. A tile with several genomes runs
+// one round per genome (the rows of other genomes are computed and discarded); a cell's
+// actuator epilogue (communication, invest/liquidate, exploration, flow quotient) runs in
+// registers in the round that computes its outputs.
 #include <cudaTypedefs.h>
 #include <math.h>
 #include <string.h>
@@ -21,7 +24,7 @@ namespace coral {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kCtasPerSm = 5;
+constexpr int kCtasPerSm = 5;                             // 5 x 64 of the 512 TMEM columns
 constexpr int kTileW = 32, kTileH = 4;
 constexpr int kHaloW = kTileW + 2, kHaloH = kTileH + 2;
 constexpr int kHaloCells = kHaloW * kHaloH;               // 204
@@ -30,13 +33,15 @@ constexpr long long kWaitCycles = 4000000000LL;           // about 2 s of SM clo
 
 // shared memory layout, offsets from a 1024-byte aligned base
 constexpr int kOffA = 0;                                  // 128 x 128 B: input tile, then hidden tile
-constexpr int kOffW = 16384;                              // genome blob (<= 10368 B)
+constexpr int kOffW = 16384;                              // genome blob (<= 10368 B at H = 64)
 // stage: float32 [6 channels][6 rows][40 columns], halo column hx at 3 + hx (the TMA box starts
-// 4 cells left of the tile so its x coordinate stays 16-byte aligned), two buffers
+// 4 cells left of the tile so its x coordinate stays 16-byte aligned). One buffer: it is free
+// again once the tile's records and each thread's own E, I and flow denominator are taken from
+// it, so the next tile's copy overlaps the current tile's network rounds.
 constexpr int kStageW = 40, kStageCh = kStageW * kHaloH;  // 240 floats per channel
 constexpr int kStageBytes = 6 * kStageCh * 4;             // 5760
-constexpr int kOffStage = kOffW + 11264;
-constexpr int kOffRec = kOffStage + 2 * kStageBytes;      // 204 x 16 B BF16 cell records
+constexpr int kOffStage = kOffW + 10368;                  // 128-byte aligned
+constexpr int kOffRec = kOffStage + kStageBytes;          // 204 x 16 B BF16 cell records
 constexpr int kOffG = kOffRec + kHaloCells * 16;          // int32 [128]
 constexpr int kOffMisc = kOffG + 512;                     // mbarrier, TMEM slot, flags
 constexpr int kSmemBytes = kOffMisc + 128 + 1024;         // + alignment slack
@@ -102,9 +107,8 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   int32_t* sG = reinterpret_cast<int32_t*>(base + kOffG);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(base + kOffMisc);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + kOffMisc + 8);
-  int* wgenome = reinterpret_cast<int*>(base + kOffMisc + 12);
-  unsigned* ballots = reinterpret_cast<unsigned*>(base + kOffMisc + 20);
-  uint64_t* halo_bar = reinterpret_cast<uint64_t*>(base + kOffMisc + 40);     // [2], one per stage
+  unsigned* ballots = reinterpret_cast<unsigned*>(base + kOffMisc + 16);      // [2][4] pending rows
+  uint64_t* halo_bar = reinterpret_cast<uint64_t*>(base + kOffMisc + 48);     // the stage's TMA barrier
   __shared__ double red_s[4][4];
   __shared__ long long red_c[4];
 
@@ -122,10 +126,8 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   }
   if (tid == 0) {
     tc::mbar_init(mbar, 1);
-    tc::mbar_init(&halo_bar[0], 1);
-    tc::mbar_init(&halo_bar[1], 1);
+    tc::mbar_init(halo_bar, 1);
     tc::fence_barrier_init();
-    *wgenome = -1;
   }
   tc::tc_fence_before();
   __syncthreads();
@@ -138,7 +140,10 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
 
   double accC[4] = {0, 0, 0, 0};
   long long accX = 0;
-  bool timed_out = false;
+  bool timed_out = false;                             // the CTA agreed to stop (a wait ran out)
+  bool bad = false;                                   // one of this thread's waits ran out
+  int staged = -1;                                    // genome whose blob is in shared memory
+  int rb = 0;                                         // ballot buffer the next round reads
   const int tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (Hh + kTileH - 1) / kTileH;
   const int n_tiles = tiles_x * tiles_y;
   // a contiguous run of tiles per CTA: neighbouring tiles share halo rows (L2) and genomes
@@ -154,23 +159,23 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     const int ch = sgm / kHaloH, hy = sgm - ch * kHaloH;
     seg_off[k] = (long long)ch * a.N + (long long)hy * W;
   }
-  uint32_t halo_phase = 0;                            // bit b: parity of halo_bar[b]
-  int tma_pending = -1;                               // stage buffer with a TMA copy in flight
+  uint32_t halo_phase = 0;                            // parity of halo_bar
+  bool tma_pending = false;                           // a TMA copy into the stage is in flight
   // A tile's halo comes by one TMA box copy when it does not wrap around the torus, else by
   // cp.async; the choice is uniform per tile.
   auto tma_tile = [&](int x0, int y0) {
     return use_tma && x0 >= 4 && x0 + kTileW + 4 <= W && y0 >= 1 && y0 + kTileH + 1 <= Hh;
   };
   // next tile: halo copy started, genome and rotation of this thread's cell loaded
-  auto prefetch = [&](int x0, int y0, int b) {
-    const uint32_t dst = base_s + kOffStage + b * kStageBytes;
+  auto prefetch = [&](int x0, int y0) {
+    const uint32_t dst = base_s + kOffStage;
     if (tma_tile(x0, y0)) {
       if (tid == 0) {
         tc::fence_proxy_async();                       // earlier generic accesses of the buffer
-        tc::mbar_expect_tx(&halo_bar[b], kStageBytes);
-        tc::tma_load_3d(dst, tmap, x0 - 4, y0 - 1, 0, &halo_bar[b]);
+        tc::mbar_expect_tx(halo_bar, kStageBytes);
+        tc::tma_load_3d(dst, tmap, x0 - 4, y0 - 1, 0, halo_bar);
       }
-      tma_pending = b;
+      tma_pending = true;
     } else {
       issue_halo(a, y0, fold(x0 - 1 + lane, W, small_w), fold(x0 + 31 + lane, W, small_w), dst, seg_off);
     }
@@ -184,12 +189,11 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     }
   };
   int tx = t_begin % tiles_x, ty = t_begin / tiles_x;   // running tile coordinates
-  if (t_begin < t_end) prefetch(tx * kTileW, ty * kTileH, 0);
+  if (t_begin < t_end) prefetch(tx * kTileW, ty * kTileH);
   float cacc[4] = {0, 0, 0, 0};           // FP32 partials of up to 8 tiles, then into accC
   int ntile = 0;
 
-  int buf = 0;
-  for (int tile = t_begin; tile < t_end; ++tile, buf ^= 1) {
+  for (int tile = t_begin; tile < t_end; ++tile) {
     const int x0 = tx * kTileW, y0 = ty * kTileH;
     if (++tx == tiles_x) {
       tx = 0;
@@ -199,21 +203,21 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     const bool valid = gx < W && gy < Hh;
     const long long j = (long long)gy * W + gx;
     const int g = g_next, r = r_next;
-    bool hok = true;
+    // this tile's halo: every thread waits on the TMA barrier itself; a cp.async tile needs
+    // the CTA barrier to see the other threads' copies
     if (tma_tile(x0, y0)) {
-      if (tid == 0) hok = tc::mbar_wait(&halo_bar[buf], (halo_phase >> buf) & 1u, kWaitCycles);
-      halo_phase ^= 1u << buf;
-      tma_pending = -1;
+      if (tc::mbar_wait(halo_bar, halo_phase, kWaitCycles)) {
+        halo_phase ^= 1u;
+        tma_pending = false;
+      } else {
+        bad = true;                                   // the copy may still land: waited for at exit
+      }
     } else {
       tc::cp_async_wait_all();
+      __syncthreads();
     }
     sG[tid] = g;
-    if (__syncthreads_or(!hok)) {                     // this tile's halo is in stage[buf]
-      timed_out = true;
-      break;
-    }
-    if (tile + 1 < t_end) prefetch(tx * kTileW, ty * kTileH, buf ^ 1);
-    const float* stage = reinterpret_cast<const float*>(base + kOffStage + buf * kStageBytes);
+    const float* stage = reinterpret_cast<const float*>(base + kOffStage);
     // BF16 records: the 6 channels of each halo cell in one 16-byte slot
     for (int c = tid; c < kHaloCells; c += kThreads) {
       const int hy = c / kHaloW;
@@ -222,36 +226,59 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
                  tc::pack_bf16x2(s[2 * kStageCh], s[3 * kStageCh]),
                  tc::pack_bf16x2(s[4 * kStageCh], s[5 * kStageCh]), 0u);
     }
+    // this cell's E and I and the FP64 sum of its 4 neighbours' I, rounded once to float32
+    float Ec, Ic, Sf;
+    {
+      const int sc = (warp + 1) * kStageW + lane + 4;  // this cell in the stage layout
+      const float* sI = stage + kStageCh;
+      Ec = stage[sc];
+      Ic = sI[sc];
+      Sf = (float)((double)sI[sc - kStageW] + (double)sI[sc + 1] + (double)sI[sc + kStageW] + (double)sI[sc - 1]);
+    }
     bool done = g < 0;
+    rb ^= 1;                                          // the last round's buffer is free again
     {
       const unsigned b = __ballot_sync(0xffffffffu, !done);   // first round's pending rows
-      if (lane == 0) ballots[warp] = b;
+      if (lane == 0) ballots[4 * rb + warp] = b;
     }
-    __syncthreads();                                  // records and the first ballots visible
+    tc::fence_proxy_async();                          // stage reads before the next tile's copy
+    if (__syncthreads_or(bad)) {                      // records and the first ballots visible
+      timed_out = true;
+      break;
+    }
+    if (tile + 1 < t_end) prefetch(tx * kTileW, ty * kTileH);
     const int hc = (warp + 1) * kHaloW + (lane + 1);
     const uint32_t row_s = a_s + tid * 128;
-    float act[kOut], zo[kOut];
+    // actuator epilogue and pass-1 stores of this thread's cell, in the round that finishes it
+    auto finish = [&](const float* act, const float* zo) {
+      CellOut o;
+      actuator_epilogue<true>(a, act, zo, Ec, Ic, Sf, r, o);
+      store_pass1(a, j, o);
 #pragma unroll
-    for (int o = 0; o < kOut; ++o) act[o] = zo[o] = 0.0f;
-    // one tensor-core round per genome present in the tile (first pending row's genome); the
-    // input rows of pending cells survive a round (only finished rows are overwritten by their
-    // hidden values), so the input tile is built once per tile
+      for (int k = 0; k < 4; ++k) cacc[k] += o.C[k];
+      accX += o.xdir != kNoExplore ? 1 : 0;
+    };
+    if (valid && g < 0) {                             // empty cell: all actuators at zero
+      const float zr[kOut] = {};
+      finish(zr, zr);
+    }
+    // One tensor-core round per genome present in the tile (the first pending row's genome).
+    // The input rows of pending cells survive a round (only finished rows are overwritten by
+    // their hidden values), so the input tile is built once per tile. Each round publishes the
+    // rows still pending after it in the other ballot buffer before its first barrier, so the
+    // tile ends without a further barrier; the MMAs' completion is awaited by every thread on
+    // the mbarrier, not through a CTA barrier.
     bool first_round = true;
     while (true) {
-      if (!first_round) {
-        const unsigned b = __ballot_sync(0xffffffffu, !done);
-        if (lane == 0) ballots[warp] = b;
-        __syncthreads();
-      }
       int first = -1;
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
-        const unsigned bw = ballots[w];
+        const unsigned bw = ballots[4 * rb + w];
         if (first < 0 && bw) first = w * 32 + __ffs(bw) - 1;
       }
       const int gs = first < 0 ? -1 : sG[first];
       if (gs < 0) break;
-      if (*wgenome != gs) {                           // stage this genome's BF16 blob
+      if (staged != gs) {                             // stage this genome's BF16 blob
         const uint4* src = reinterpret_cast<const uint4*>(a.nets16 + (long long)gs * a.blob_bytes);
         const int n16 = a.blob_bytes >> 4;             // <= 648 = 6 x 108 per thread slot
 #pragma unroll
@@ -268,6 +295,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
             if (i < n16) tc::sts128(w_s + i * 16, v[k].x, v[k].y, v[k].z, v[k].w);
           }
         }
+        staged = gs;
       }
       // this cell's input row: chunk p = the record of kernel rank p (p < 8) whose spare 4th
       // word carries rank 8's channels (p < 3) or the bias 1.0 (p = 3); 128-byte swizzle.
@@ -277,7 +305,6 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
         const unsigned long long offs = r == 0 ? rank_offsets(0) : r == 1 ? rank_offsets(1)
                                       : r == 2 ? rank_offsets(2) : rank_offsets(3);
         const uint4 r8 = tc::lds128(c_s + (int)(int8_t)(uint8_t)(offs >> 56) * 16);
-        const uint32_t row_s = a_s + tid * 128;
         const uint32_t t7 = tid & 7;
         uint4 rc = tc::lds128(c_s);
         tc::sts128(row_s + ((0u ^ t7) << 4), rc.x, rc.y, rc.z, r8.x);
@@ -289,32 +316,35 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
           tc::sts128(row_s + (((uint32_t)p ^ t7) << 4), rc.x, rc.y, rc.z, w4);
         }
       }
+      const bool mine = !done && g == gs;
+      {
+        const unsigned b = __ballot_sync(0xffffffffu, !done && !mine);   // pending after this round
+        if (lane == 0) ballots[4 * (rb ^ 1) + warp] = b;
+      }
       tc::fence_proxy_async();
-      __syncthreads();
-      bool ok = true;
-      if (tid == 0) {          // one thread issues and waits; the others park at the barrier
-        *wgenome = gs;
+      if (__syncthreads_or(bad)) {
+        timed_out = true;
+        break;
+      }
+      if (tid == 0) {
         tc::tc_fence_after();
         const uint64_t ad = tc::sdesc_sw128(a_s), bd = tc::sdesc_sw128(w_s);
 #pragma unroll
         for (int k = 0; k < 4; ++k) tc::mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc1, k > 0);
         tc::mma_commit(mbar);
-        ok = tc::mbar_wait(mbar, phase, kWaitCycles);
       }
+      if (!tc::mbar_wait(mbar, phase, kWaitCycles)) bad = true;
       phase ^= 1;
-      if (__syncthreads_or(!ok)) { timed_out = true; break; }
       tc::tc_fence_after();
-      const bool mine = !done && g == gs;
       if (H == 0) {
         float v[16];
         tc::tmem_ld16(t_lane, v);
         tc::tmem_wait_ld();
         if (mine) {
+          float act[kOut];
 #pragma unroll
-          for (int o = 0; o < kOut; ++o) {
-            zo[o] = v[o];
-            act[o] = tc::tanh_approx(v[o]);
-          }
+          for (int o = 0; o < kOut; ++o) act[o] = tc::tanh_approx(v[o]);
+          finish(act, v);
         }
       } else {
         // hidden layer: tanh, BF16, written over this row of the (consumed) input tile
@@ -332,50 +362,39 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
         }
         tc::fence_proxy_async();
         tc::tc_fence_before();
-        __syncthreads();
+        if (__syncthreads_or(bad)) {
+          timed_out = true;
+          break;
+        }
         if (tid == 0) {
           tc::tc_fence_after();
           const uint64_t ad = tc::sdesc_sw128(a_s), bd = tc::sdesc_sw128(w_s + bf16_w2_off(H));
           for (int k = 0; k < N1 / 16; ++k) tc::mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc2, k > 0);
           tc::mma_commit(mbar);
-          ok = tc::mbar_wait(mbar, phase, kWaitCycles);
         }
+        if (!tc::mbar_wait(mbar, phase, kWaitCycles)) bad = true;
         phase ^= 1;
-        if (__syncthreads_or(!ok)) { timed_out = true; break; }
         tc::tc_fence_after();
         float v[16];
         tc::tmem_ld16(t_lane, v);
         tc::tmem_wait_ld();
         if (mine) {
           const float* b2 = reinterpret_cast<const float*>(base + kOffW + bf16_b2_off(H));
+          float act[kOut];
 #pragma unroll
           for (int o = 0; o < kOut; ++o) {
-            zo[o] = v[o] + b2[o];
-            act[o] = tc::tanh_approx(zo[o]);
+            v[o] += b2[o];
+            act[o] = tc::tanh_approx(v[o]);
           }
+          finish(act, v);
         }
       }
       tc::tc_fence_before();
       if (mine) done = true;
       first_round = false;
+      rb ^= 1;
     }
     if (timed_out) break;
-    // actuator epilogue and pass-1 stores
-    CellOut o;
-    o.C[0] = o.C[1] = o.C[2] = o.C[3] = 0.0f;
-    o.xdir = kNoExplore;
-    if (valid) {
-      const int sc = (warp + 1) * kStageW + lane + 4;  // this cell in the stage layout
-      const float* sI = stage + kStageCh;
-      const double S = (double)sI[sc - kStageW] + (double)sI[sc + 1] + (double)sI[sc + kStageW] + (double)sI[sc - 1];
-      actuator_epilogue<true>(a, act, zo, stage[sc], sI[sc], (float)S, r, o);
-      store_pass1(a, j, o);
-    }
-    if (valid) {
-#pragma unroll
-      for (int k = 0; k < 4; ++k) cacc[k] += o.C[k];
-      accX += o.xdir != kNoExplore ? 1 : 0;
-    }
     if (++ntile == 8) {
       ntile = 0;
 #pragma unroll
@@ -386,10 +405,8 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     }
   }
   tc::cp_async_wait_all();                            // no copy may land after the CTA exits
-  if (tid == 0 && tma_pending >= 0)
-    tc::mbar_wait(&halo_bar[tma_pending], (halo_phase >> tma_pending) & 1u, kWaitCycles);
+  if (tid == 0 && tma_pending) tc::mbar_wait(halo_bar, halo_phase, kWaitCycles);
 
-  if (timed_out && tid == 0) atomicCAS(a.status, 0, (int)CORAL_E_TIMEOUT);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     double v = accC[k] + (double)cacc[k];
@@ -406,7 +423,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     red_c[warp] = accX;
   }
   tc::tc_fence_before();
-  __syncthreads();
+  if (__syncthreads_or(bad || timed_out) && tid == 0) atomicCAS(a.status, 0, (int)CORAL_E_TIMEOUT);
   if (tid == 0) {
     Partial p = {};
     for (int w = 0; w < 4; ++w) {
