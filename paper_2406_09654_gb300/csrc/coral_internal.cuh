@@ -167,8 +167,9 @@ __host__ __device__ inline void octant_offset(int o, int& dx, int& dy) {
   dy = (int)((0x1A90u >> (2 * o)) & 3u) - 1;
 }
 
-// Explore logit k -> quarter turns clockwise from the forward direction (fwd, right, left, back).
-__host__ __device__ constexpr int explore_turn(int k) { return k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 3 : 2; }
+// Explore logit k -> quarter turns clockwise from the forward direction (fwd, right, left, back):
+// 0, 1, 3, 2, which is the Gray code of k (two integer operations, no table).
+__host__ __device__ constexpr int explore_turn(int k) { return k ^ (k >> 1); }
 
 // ---- reductions: FP32 within a warp (32 cells), FP64 above ------------------------------
 __device__ inline float warp_sum(float v) {

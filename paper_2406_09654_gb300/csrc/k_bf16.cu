@@ -44,7 +44,8 @@ constexpr int kOffStage = kOffW + 10368;                  // 128-byte aligned
 constexpr int kOffRec = kOffStage + kStageBytes;          // 204 x 16 B BF16 cell records
 constexpr int kOffG = kOffRec + kHaloCells * 16;          // int32 [128]
 constexpr int kOffMisc = kOffG + 512;                     // mbarrier, TMEM slot, flags
-constexpr int kSmemBytes = kOffMisc + 128 + 1024;         // + alignment slack
+constexpr int kOffAcc = kOffMisc + 128;                   // double [4][128]: per-thread sums of C'
+constexpr int kSmemBytes = kOffAcc + 4 * kThreads * 8 + 1024;  // + alignment slack
 
 // v in [-1, n + tile) folded onto [0, n): one conditional step when the torus side is at least
 // the halo's (small), else a full modulo.
@@ -71,23 +72,17 @@ __host__ __device__ constexpr unsigned long long rank_offsets(int r) {
 // Starts the asynchronous copy (cp.async, for tiles whose halo wraps around the torus) of a
 // tile's 34 x 6 halo of the six contiguous sensor planes into a stage buffer: warp w copies row
 // segments w, w+4, ... (one per channel and halo row); lane l copies column l, lanes 0 and 1
-// also columns 32 and 33. seg_off[k]: channel * N + halo-row * W of this warp's k-th segment
-// (no vertical wrap); col_a / col_b: the wrapped grid columns of this lane's halo column(s).
-__device__ __forceinline__ void issue_halo(const StepArgs& a, int y0, int col_a, int col_b, uint32_t dst,
-                                           const long long* seg_off) {
+// also columns 32 and 33. col_a / col_b: the wrapped grid columns of this lane's halo column(s).
+__device__ __forceinline__ void issue_halo(const StepArgs& a, int y0, int col_a, int col_b, uint32_t dst) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool wraps = y0 == 0 || y0 - 1 + kHaloH > a.H;
-  const long long row0 = (long long)(y0 - 1) * a.W;
   const bool small_h = a.H < kHaloH;
 #pragma unroll
   for (int k = 0; k < 6 * kHaloH / (kThreads / 32); ++k) {
     const int sgm = warp + k * (kThreads / 32);
     const int ch = sgm / kHaloH, hy = sgm - ch * kHaloH;
-    long long off;
-    if (!wraps)
-      off = seg_off[k] + row0;
-    else
-      off = (long long)ch * a.N + (long long)fold(y0 - 1 + hy, a.H, small_h) * a.W;
+    const int gy = wraps ? fold(y0 - 1 + hy, a.H, small_h) : y0 - 1 + hy;
+    const long long off = (long long)ch * a.N + (long long)gy * a.W;
     const float* row = a.cur.E + off;
     const uint32_t d = dst + 4u * (uint32_t)(ch * kStageCh + hy * kStageW + 3);
     tc::cp_async4(d + 4u * lane, row + col_a);
@@ -109,6 +104,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + kOffMisc + 8);
   unsigned* ballots = reinterpret_cast<unsigned*>(base + kOffMisc + 16);      // [2][4] pending rows
   uint64_t* halo_bar = reinterpret_cast<uint64_t*>(base + kOffMisc + 48);     // the stage's TMA barrier
+  unsigned* match = reinterpret_cast<unsigned*>(base + kOffMisc + 64);        // [4] rows of the staged genome
   __shared__ double red_s[4][4];
   __shared__ long long red_c[4];
 
@@ -138,8 +134,10 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   const uint32_t idesc2 = tc::idesc_bf16_f32(128, 16);
   uint32_t phase = 0;
 
-  double accC[4] = {0, 0, 0, 0};
-  long long accX = 0;
+  double* accC = reinterpret_cast<double*>(base + kOffAcc) + tid;   // [k * kThreads]: FP64 sums
+#pragma unroll
+  for (int k = 0; k < 4; ++k) accC[k * kThreads] = 0.0;
+  int accX = 0;
   bool timed_out = false;                             // the CTA agreed to stop (a wait ran out)
   bool bad = false;                                   // one of this thread's waits ran out
   int staged = -1;                                    // genome whose blob is in shared memory
@@ -152,13 +150,6 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   const int t_end = t_begin + per < n_tiles ? t_begin + per : n_tiles;
   int g_next = -1, r_next = 0;
   const bool small_w = W < kHaloW;
-  long long seg_off[6 * kHaloH / (kThreads / 32)];   // this warp's segments: ch * N + hy * W
-#pragma unroll
-  for (int k = 0; k < 6 * kHaloH / (kThreads / 32); ++k) {
-    const int sgm = warp + k * (kThreads / 32);
-    const int ch = sgm / kHaloH, hy = sgm - ch * kHaloH;
-    seg_off[k] = (long long)ch * a.N + (long long)hy * W;
-  }
   uint32_t halo_phase = 0;                            // parity of halo_bar
   bool tma_pending = false;                           // a TMA copy into the stage is in flight
   // A tile's halo comes by one TMA box copy when it does not wrap around the torus, else by
@@ -177,7 +168,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       }
       tma_pending = true;
     } else {
-      issue_halo(a, y0, fold(x0 - 1 + lane, W, small_w), fold(x0 + 31 + lane, W, small_w), dst, seg_off);
+      issue_halo(a, y0, fold(x0 - 1 + lane, W, small_w), fold(x0 + 31 + lane, W, small_w), dst);
     }
     g_next = -1;
     r_next = 0;
@@ -240,6 +231,8 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     {
       const unsigned b = __ballot_sync(0xffffffffu, !done);   // first round's pending rows
       if (lane == 0) ballots[4 * rb + warp] = b;
+      const unsigned m = __ballot_sync(0xffffffffu, !done && g == staged);   // rows of the staged genome
+      if (lane == 0) match[warp] = m;
     }
     tc::fence_proxy_async();                          // stage reads before the next tile's copy
     if (__syncthreads_or(bad)) {                      // records and the first ballots visible
@@ -262,7 +255,8 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       const float zr[kOut] = {};
       finish(zr, zr);
     }
-    // One tensor-core round per genome present in the tile (the first pending row's genome).
+    // One tensor-core round per genome present in the tile: first the genome whose blob is
+    // already staged, if the tile has cells of it, then the first pending row's genome.
     // The input rows of pending cells survive a round (only finished rows are overwritten by
     // their hidden values), so the input tile is built once per tile. Each round publishes the
     // rows still pending after it in the other ballot buffer before its first barrier, so the
@@ -270,13 +264,14 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     // the mbarrier, not through a CTA barrier.
     bool first_round = true;
     while (true) {
-      int first = -1;
-#pragma unroll
-      for (int w = 0; w < 4; ++w) {
-        const unsigned bw = ballots[4 * rb + w];
-        if (first < 0 && bw) first = w * 32 + __ffs(bw) - 1;
+      const uint4 bl = *reinterpret_cast<const uint4*>(ballots + 4 * rb);
+      const int first = bl.x ? __ffs(bl.x) - 1 : bl.y ? 31 + __ffs(bl.y) : bl.z ? 63 + __ffs(bl.z)
+                      : bl.w ? 95 + __ffs(bl.w) : -1;
+      int gs = first < 0 ? -1 : sG[first];
+      if (first_round) {                              // the staged genome first: no restaging
+        const uint4 mt = *reinterpret_cast<const uint4*>(match);
+        if (mt.x | mt.y | mt.z | mt.w) gs = staged;
       }
-      const int gs = first < 0 ? -1 : sG[first];
       if (gs < 0) break;
       if (staged != gs) {                             // stage this genome's BF16 blob
         const uint4* src = reinterpret_cast<const uint4*>(a.nets16 + (long long)gs * a.blob_bytes);
@@ -399,7 +394,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       ntile = 0;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        accC[k] += (double)cacc[k];
+        accC[k * kThreads] += (double)cacc[k];
         cacc[k] = 0.0f;
       }
     }
@@ -409,19 +404,15 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
 
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    double v = accC[k] + (double)cacc[k];
+    double v = accC[k * kThreads] + (double)cacc[k];
 #pragma unroll
     for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    accC[k] = v;
+    if (lane == 0) red_s[warp][k] = v;
   }
-  long long ex = accX;
+  int ex = accX;
 #pragma unroll
   for (int off = 16; off; off >>= 1) ex += __shfl_xor_sync(0xffffffffu, ex, off);
-  accX = ex;
-  if (lane == 0) {
-    for (int k = 0; k < 4; ++k) red_s[warp][k] = accC[k];
-    red_c[warp] = accX;
-  }
+  if (lane == 0) red_c[warp] = ex;
   tc::tc_fence_before();
   if (__syncthreads_or(bad || timed_out) && tid == 0) atomicCAS(a.status, 0, (int)CORAL_E_TIMEOUT);
   if (tid == 0) {
