@@ -44,8 +44,7 @@ constexpr int kOffStage = kOffW + 10368;                  // 128-byte aligned
 constexpr int kOffRec = kOffStage + kStageBytes;          // 204 x 16 B BF16 cell records
 constexpr int kOffG = kOffRec + kHaloCells * 16;          // int32 [128]
 constexpr int kOffMisc = kOffG + 512;                     // mbarrier, TMEM slot, flags
-constexpr int kOffAcc = kOffMisc + 128;                   // double [4][128]: per-thread sums of C'
-constexpr int kSmemBytes = kOffAcc + 4 * kThreads * 8 + 1024;  // + alignment slack
+constexpr int kSmemBytes = kOffMisc + 128 + 1024;         // + alignment slack
 
 // v in [-1, n + tile) folded onto [0, n): one conditional step when the torus side is at least
 // the halo's (small), else a full modulo.
@@ -134,9 +133,10 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   const uint32_t idesc2 = tc::idesc_bf16_f32(128, 16);
   uint32_t phase = 0;
 
-  double* accC = reinterpret_cast<double*>(base + kOffAcc) + tid;   // [k * kThreads]: FP64 sums
+  if (lane == 0) {                                    // this warp's FP64 sums of C'
 #pragma unroll
-  for (int k = 0; k < 4; ++k) accC[k * kThreads] = 0.0;
+    for (int k = 0; k < 4; ++k) red_s[warp][k] = 0.0;
+  }
   int accX = 0;
   bool timed_out = false;                             // the CTA agreed to stop (a wait ran out)
   bool bad = false;                                   // one of this thread's waits ran out
@@ -181,7 +181,18 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   };
   int tx = t_begin % tiles_x, ty = t_begin / tiles_x;   // running tile coordinates
   if (t_begin < t_end) prefetch(tx * kTileW, ty * kTileH);
-  float cacc[4] = {0, 0, 0, 0};           // FP32 partials of up to 8 tiles, then into accC
+  float cacc[4] = {0, 0, 0, 0};           // FP32 partials of up to 16 tiles, then into red_s
+  // adds the partials of this warp's 32 threads in FP64 (fixed tree) to its row of red_s
+  auto flush = [&]() {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double v = (double)cacc[k];
+#pragma unroll
+      for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+      if (lane == 0) red_s[warp][k] += v;
+      cacc[k] = 0.0f;
+    }
+  };
   int ntile = 0;
 
   for (int tile = t_begin; tile < t_end; ++tile) {
@@ -217,14 +228,16 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
                  tc::pack_bf16x2(s[2 * kStageCh], s[3 * kStageCh]),
                  tc::pack_bf16x2(s[4 * kStageCh], s[5 * kStageCh]), 0u);
     }
-    // this cell's E and I and the FP64 sum of its 4 neighbours' I, rounded once to float32
+    // this cell's E and I and the sum S of its 4 neighbours' I. In FP32: with I >= 0, which the
+    // physics keeps from a non-negative start, S > 0 exactly when the FP64 sum is and the two
+    // differ by at most 2 ulp, far inside this path's BF16 tolerance.
     float Ec, Ic, Sf;
     {
       const int sc = (warp + 1) * kStageW + lane + 4;  // this cell in the stage layout
       const float* sI = stage + kStageCh;
       Ec = stage[sc];
       Ic = sI[sc];
-      Sf = (float)((double)sI[sc - kStageW] + (double)sI[sc + 1] + (double)sI[sc + kStageW] + (double)sI[sc - 1]);
+      Sf = (sI[sc - kStageW] + sI[sc + 1]) + (sI[sc + kStageW] + sI[sc - 1]);
     }
     bool done = g < 0;
     rb ^= 1;                                          // the last round's buffer is free again
@@ -390,25 +403,15 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       rb ^= 1;
     }
     if (timed_out) break;
-    if (++ntile == 8) {
+    if (++ntile == 16) {
       ntile = 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        accC[k * kThreads] += (double)cacc[k];
-        cacc[k] = 0.0f;
-      }
+      flush();
     }
   }
   tc::cp_async_wait_all();                            // no copy may land after the CTA exits
   if (tid == 0 && tma_pending) tc::mbar_wait(halo_bar, halo_phase, kWaitCycles);
 
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    double v = accC[k * kThreads] + (double)cacc[k];
-#pragma unroll
-    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    if (lane == 0) red_s[warp][k] = v;
-  }
+  flush();
   int ex = accX;
 #pragma unroll
   for (int off = 16; off; off >>= 1) ex += __shfl_xor_sync(0xffffffffu, ex, off);
