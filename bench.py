@@ -397,7 +397,7 @@ def run_coral(a, rank, world_size, local):
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world_size,
         "steps": a.steps, "warmup": a.warmup, "ms_per_step": total_ms / a.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype":
-            "bf16 network operands, f32 accumulation, state and flow sums, f64 totals" if path == "bf16"
+            "bf16 network operands, f32 accumulation and state, f64 flow sums and totals" if path == "bf16"
             else "f32 (f64 flow sums and totals)",
         "data": "synthetic (seeded world generator; the paper has no dataset)",
         "config": {"workload": f"{a.workload}: {WORKLOADS[a.workload]}", "path": path, "width": w.width,

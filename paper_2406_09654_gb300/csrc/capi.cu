@@ -671,7 +671,7 @@ BatchTable table_of(const coral_batch* b) {
 int batch_configure(coral_batch* b) {
   std::vector<long long> tiles, cells;
   for (coral_substrate* s : b->worlds) {
-    tiles.push_back((long long)((s->W + 31) / 32) * ((s->H + 3) / 4));
+    tiles.push_back(pass1_bf16_tiles(s->W, s->H));
     cells.push_back(s->N);
   }
   std::vector<int> cw1, f1, c1, cw2, f2, c2;

@@ -210,6 +210,7 @@ cudaError_t launch_selftest_wait(long long max_cycles, int* status, cudaStream_t
 int pass1_bf16_grid(int sms);
 int pass2_grid(int sms);
 size_t pass1_bf16_smem();
+long long pass1_bf16_tiles(int W, int H);   // tensor-core pass-1 tiles of a W x H world
 
 struct GenomeArgs {
   int hidden;

@@ -25,9 +25,9 @@ namespace {
 
 constexpr int kThreads = 128;
 constexpr int kCtasPerSm = 5;                             // 5 x 64 of the 512 TMEM columns
-constexpr int kTileW = 32, kTileH = 4;
+constexpr int kTileW = 32, kTileH = kThreads / kTileW;   // thread q: cell (q % kTileW, q / kTileW)
 constexpr int kHaloW = kTileW + 2, kHaloH = kTileH + 2;
-constexpr int kHaloCells = kHaloW * kHaloH;               // 204
+constexpr int kHaloCells = kHaloW * kHaloH;
 constexpr uint32_t kTmemCols = 64;                        // layer 1, then layer 2 in cols 0..15
 constexpr long long kWaitCycles = 4000000000LL;           // about 2 s of SM clock
 
@@ -38,7 +38,7 @@ constexpr int kOffW = 16384;                              // genome blob (<= 103
 // 4 cells left of the tile so its x coordinate stays 16-byte aligned). One buffer: it is free
 // again once the tile's records and each thread's own E, I and flow denominator are taken from
 // it, so the next tile's copy overlaps the current tile's network rounds.
-constexpr int kStageW = 40, kStageCh = kStageW * kHaloH;  // 240 floats per channel
+constexpr int kStageW = kTileW + 8, kStageCh = kStageW * kHaloH;  // 240 floats per channel
 constexpr int kStageBytes = 6 * kStageCh * 4;             // 5760
 constexpr int kOffStage = kOffW + 10368;                  // 128-byte aligned
 constexpr int kOffRec = kOffStage + kStageBytes;          // 204 x 16 B BF16 cell records
@@ -69,13 +69,15 @@ __host__ __device__ constexpr unsigned long long rank_offsets(int r) {
 }
 
 // Starts the asynchronous copy (cp.async, for tiles whose halo wraps around the torus) of a
-// tile's 34 x 6 halo of the six contiguous sensor planes into a stage buffer: warp w copies row
-// segments w, w+4, ... (one per channel and halo row); lane l copies column l, lanes 0 and 1
-// also columns 32 and 33. col_a / col_b: the wrapped grid columns of this lane's halo column(s).
-__device__ __forceinline__ void issue_halo(const StepArgs& a, int y0, int col_a, int col_b, uint32_t dst) {
+// tile's halo of the six contiguous sensor planes into a stage buffer: warp w copies row
+// segments w, w+4, ... (one per channel and halo row); lane l copies halo columns l and l + 32.
+__device__ __forceinline__ void issue_halo(const StepArgs& a, int x0, int y0, uint32_t dst) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool wraps = y0 == 0 || y0 - 1 + kHaloH > a.H;
-  const bool small_h = a.H < kHaloH;
+  const bool small_h = a.H < kHaloH, small_w = a.W < kHaloW;
+  const int col_a = fold(x0 - 1 + lane, a.W, small_w);
+  const int col_b = fold(x0 + 31 + lane, a.W, small_w);
+  static_assert(kHaloW <= 64 && (6 * kHaloH) % (kThreads / 32) == 0, "halo copy layout");
 #pragma unroll
   for (int k = 0; k < 6 * kHaloH / (kThreads / 32); ++k) {
     const int sgm = warp + k * (kThreads / 32);
@@ -84,8 +86,8 @@ __device__ __forceinline__ void issue_halo(const StepArgs& a, int y0, int col_a,
     const long long off = (long long)ch * a.N + (long long)gy * a.W;
     const float* row = a.cur.E + off;
     const uint32_t d = dst + 4u * (uint32_t)(ch * kStageCh + hy * kStageW + 3);
-    tc::cp_async4(d + 4u * lane, row + col_a);
-    if (lane < 2) tc::cp_async4(d + 4u * (32 + lane), row + col_b);
+    if (lane < kHaloW) tc::cp_async4(d + 4u * lane, row + col_a);
+    if (lane + 32 < kHaloW) tc::cp_async4(d + 4u * (32 + lane), row + col_b);
   }
   tc::cp_async_commit();
 }
@@ -108,6 +110,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   __shared__ long long red_c[4];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int lx = tid % kTileW, ly = tid / kTileW;     // this thread's cell within a tile
   const int W = a.W, Hh = a.H;
   const int H = a.hidden;
   const int N1 = H ? H : 16;
@@ -149,7 +152,6 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   const int t_begin = cta * per;
   const int t_end = t_begin + per < n_tiles ? t_begin + per : n_tiles;
   int g_next = -1, r_next = 0;
-  const bool small_w = W < kHaloW;
   uint32_t halo_phase = 0;                            // parity of halo_bar
   bool tma_pending = false;                           // a TMA copy into the stage is in flight
   // A tile's halo comes by one TMA box copy when it does not wrap around the torus, else by
@@ -168,11 +170,11 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       }
       tma_pending = true;
     } else {
-      issue_halo(a, y0, fold(x0 - 1 + lane, W, small_w), fold(x0 + 31 + lane, W, small_w), dst);
+      issue_halo(a, x0, y0, dst);
     }
     g_next = -1;
     r_next = 0;
-    const int gx = x0 + lane, gy = y0 + warp;
+    const int gx = x0 + lx, gy = y0 + ly;
     if (gx < W && gy < Hh) {
       const int jn = gy * W + gx;
       g_next = __ldg(a.cur.G + jn);
@@ -201,7 +203,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       tx = 0;
       ++ty;
     }
-    const int gx = x0 + lane, gy = y0 + warp;
+    const int gx = x0 + lx, gy = y0 + ly;
     const bool valid = gx < W && gy < Hh;
     const long long j = (long long)gy * W + gx;
     const int g = g_next, r = r_next;
@@ -228,16 +230,14 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
                  tc::pack_bf16x2(s[2 * kStageCh], s[3 * kStageCh]),
                  tc::pack_bf16x2(s[4 * kStageCh], s[5 * kStageCh]), 0u);
     }
-    // this cell's E and I and the sum S of its 4 neighbours' I. In FP32: with I >= 0, which the
-    // physics keeps from a non-negative start, S > 0 exactly when the FP64 sum is and the two
-    // differ by at most 2 ulp, far inside this path's BF16 tolerance.
+    // this cell's E and I and the FP64 sum S of its 4 neighbours' I (N, E, S, W), rounded once
     float Ec, Ic, Sf;
     {
-      const int sc = (warp + 1) * kStageW + lane + 4;  // this cell in the stage layout
+      const int sc = (ly + 1) * kStageW + lx + 4;      // this cell in the stage layout
       const float* sI = stage + kStageCh;
       Ec = stage[sc];
       Ic = sI[sc];
-      Sf = (sI[sc - kStageW] + sI[sc + 1]) + (sI[sc + kStageW] + sI[sc - 1]);
+      Sf = (float)((double)sI[sc - kStageW] + (double)sI[sc + 1] + (double)sI[sc + kStageW] + (double)sI[sc - 1]);
     }
     bool done = g < 0;
     rb ^= 1;                                          // the last round's buffer is free again
@@ -253,7 +253,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       break;
     }
     if (tile + 1 < t_end) prefetch(tx * kTileW, ty * kTileH);
-    const int hc = (warp + 1) * kHaloW + (lane + 1);
+    const int hc = (ly + 1) * kHaloW + (lx + 1);
     const uint32_t row_s = a_s + tid * 128;
     // actuator epilogue and pass-1 stores of this thread's cell, in the round that finishes it
     auto finish = [&](const float* act, const float* zo) {
@@ -482,6 +482,10 @@ cudaError_t launch_selftest_wait(long long max_cycles, int* status, cudaStream_t
 }
 
 size_t pass1_bf16_smem() { return kSmemBytes; }
+
+long long pass1_bf16_tiles(int W, int H) {
+  return (long long)((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH);
+}
 
 int pass1_bf16_grid(int sms) {
   int dev = 0, major = 0;
