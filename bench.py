@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--path", default="auto", choices=["auto", "bf16", "fp32"])
     ap.add_argument("--workload", default="cfg3", choices=list(WORKLOADS))
     ap.add_argument("--fp32-steps", type=int, default=12, help="steps of the FP32 comparison run")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batched-steps", type=int, default=10, help="steps of the 256-world batch (0 = skip)")
@@ -365,22 +365,15 @@ def run_coral(a, rank, world_size, local):
         nbytes = STATE_BYTES * N
         host = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
         sub.read_channels(coral.CH_ALL, out=host)
-        hv = host.numpy()
-        E = hv[0:4 * N].view(np.float32)
-        I = hv[4 * N:8 * N].view(np.float32)
-        C = hv[8 * N:24 * N].view(np.float32)
-        G = hv[24 * N:28 * N].view(np.int32)
-        R = hv[28 * N:29 * N]
         t = sub.get_step()
+        # each step is one job of coral_step_jobs: the state copied in from pinned host
+        # memory, one step, the result copied out; consecutive jobs' copies overlap the steps
+        out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        sub.step_jobs([host], [out], 1, t)                      # staging buffers, first use
         torch.cuda.synchronize()
         barrier(world_size)
         t0 = time.perf_counter()
-        for _ in range(a.e2e_steps):
-            sub.load_state(E, I, C, G, R)
-            sub.set_step(t)
-            sub.step(1)
-            sub.read_channels(coral.CH_ALL, out=host)
-            t += 1
+        sub.step_jobs([host] * a.e2e_steps, [out] * a.e2e_steps, 1, t)
         el = max_over_ranks(time.perf_counter() - t0, world_size)
         e2e = {"value": N * a.e2e_steps * world_size / el, "unit": "cell-updates/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}

@@ -178,6 +178,26 @@ int coral_step_timed(coral_substrate* s, int32_t n_steps, float* step_ms, float*
 int coral_read_channels(coral_substrate* s, uint32_t channel_mask, void* dst, size_t dst_bytes,
                         int dst_on_device);
 
+/*
+ * Steps a sequence of independent states ("jobs") of this substrate's world from host memory
+ * to host memory. Job k's state is read from host_in[k], loaded, validated like
+ * coral_state_load, stepped n_steps times starting at step index t0 (so every job sees the same
+ * day/night phase and radiation schedule), and the resulting state is written to host_out[k].
+ * A state is packed like coral_read_channels with CORAL_CH_ALL: E, I, C0..C3 as float32 [N],
+ * G as int32 [N], R as uint8 [N] (29 bytes per cell). An input buffer must not overlap an
+ * output buffer; all host_in[k] may be one shared read-only buffer and all host_out[k] one
+ * shared buffer (written in job order). The copy in of job k+1, the steps of
+ * job k and the copy out of job k-1 run concurrently on separate CUDA streams through two pairs
+ * of device staging buffers (allocated at the first call, 4 x 29 bytes per cell, kept until
+ * destroy); page-locked host buffers let the copies overlap. Returns after every result is in
+ * host memory; the substrate's own state is then the last job's result and its step counter
+ * t0 + n_steps. Errors: E_INVALID for bad arguments or an invalid G/R in any input (reported
+ * after all jobs ran), E_OOM, E_CUDA. The paper has no counterpart: this is the library's
+ * host-to-host stepping path, used for the end-to-end throughput.
+ */
+int coral_step_jobs(coral_substrate* s, int32_t n_jobs, const void* const* host_in, void* const* host_out,
+                    int32_t n_steps, int64_t t0);
+
 /* Copies up to n stats records starting at step step_from (steps older than the ring's
  * 4096-step window are gone: E_INVALID). Host memory. Synchronises. */
 int coral_read_stats(coral_substrate* s, int64_t step_from, int32_t n, coral_stats* out);

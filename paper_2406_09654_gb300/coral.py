@@ -57,6 +57,8 @@ class Stats(ctypes.Structure):
 
 
 _VP, _I32, _I64, _U32, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32, ctypes.c_size_t
+STATE_BYTES = 29     # packed state per cell: E, I, C0..C3 float32, G int32, R uint8
+
 SIGNATURES = {
     "coral_params_default": (ctypes.c_int, [ctypes.POINTER(Params)]),
     "coral_substrate_create": (ctypes.c_int, [ctypes.POINTER(Params), _I32, _I32, _I32, _VP,
@@ -67,6 +69,7 @@ SIGNATURES = {
     "coral_cppn_generate_weights": (ctypes.c_int, [_VP, _VP, _I32]),
     "coral_step": (ctypes.c_int, [_VP, _I32]),
     "coral_step_timed": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
+    "coral_step_jobs": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I32, _I64]),
     "coral_read_channels": (ctypes.c_int, [_VP, _U32, _VP, _SZ, ctypes.c_int]),
     "coral_read_stats": (ctypes.c_int, [_VP, _I64, _I32, ctypes.POINTER(Stats)]),
     "coral_read_perm": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -231,6 +234,26 @@ class Substrate:
     # -- stepping
     def step(self, n=1):
         _check(lib().coral_step(self.h, int(n)), self.h)
+
+    def step_jobs(self, host_in, host_out, n_steps=1, t0=0):
+        """Host-to-host stepping of independent states (coral_step_jobs): host_in / host_out
+        are equal-length lists of packed-state buffers (29 bytes per cell, CH_ALL order; numpy
+        arrays or CPU tensors, ideally pinned). Copies overlap with the steps."""
+        if len(host_in) != len(host_out):
+            raise ValueError("host_in and host_out must have the same length")
+        need = STATE_BYTES * self.n
+        ptrs_in, ptrs_out = [], []
+        for bufs, ptrs in ((host_in, ptrs_in), (host_out, ptrs_out)):
+            for b in bufs:
+                p, dev = _ptr(b)
+                size = b.nbytes if isinstance(b, np.ndarray) else b.numel() * b.element_size()
+                if dev or size < need:
+                    raise ValueError(f"job buffers must be host memory of at least {need} bytes")
+                ptrs.append(p)
+        k = len(ptrs_in)
+        arr_in = (_VP * max(k, 1))(*ptrs_in)
+        arr_out = (_VP * max(k, 1))(*ptrs_out)
+        _check(lib().coral_step_jobs(self.h, k, arr_in, arr_out, int(n_steps), int(t0)), self.h)
 
     def step_timed(self, n=1):
         """Steps with CUDA-event timing; returns (step_ms [n], stage_ms [n][3])."""

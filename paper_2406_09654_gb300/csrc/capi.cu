@@ -12,6 +12,17 @@
 
 using namespace coral;
 
+// Host-to-host job stepping (coral_step_jobs): two input and two output staging buffers of
+// one packed state each, a copy-in and a copy-out stream, and the events that order them with
+// the substrate's stream. Created at the first call.
+struct JobPipe {
+  uint8_t* in[2] = {};
+  uint8_t* out[2] = {};
+  cudaStream_t s_in = nullptr, s_out = nullptr;
+  cudaEvent_t h2d_done[2] = {}, in_free[2] = {}, out_ready[2] = {}, out_free[2] = {};
+  bool ready = false;
+};
+
 struct coral_substrate {
   coral_params p;
   int W = 0, H = 0;
@@ -46,6 +57,7 @@ struct coral_substrate {
   int32_t* sort_buf = nullptr;
   long long t = 0;
   int grid1 = 0, grid2 = 0;
+  JobPipe jobs;
   std::string err;
 };
 
@@ -263,6 +275,15 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
 int coral_substrate_destroy(coral_substrate* s) {
   if (!s) return CORAL_OK;
   cudaStreamSynchronize(s->stream);
+  JobPipe& jp = s->jobs;
+  for (cudaStream_t st : {jp.s_in, jp.s_out})
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+  for (int b = 0; b < 2; ++b)
+    for (cudaEvent_t ev : {jp.h2d_done[b], jp.in_free[b], jp.out_ready[b], jp.out_free[b]})
+      if (ev) cudaEventDestroy(ev);
   free_all(s);
   delete s;
   return CORAL_OK;
@@ -399,6 +420,84 @@ extern "C" int coral_step(coral_substrate* s, int32_t n_steps) {
   for (int i = 0; i < n_steps; ++i)
     if ((rc = enqueue_step(s, nullptr)) != CORAL_OK) return rc;
   return CORAL_OK;
+}
+
+namespace {
+
+int jobs_setup(coral_substrate* s) {
+  JobPipe& jp = s->jobs;
+  if (jp.ready) return CORAL_OK;
+  const size_t bytes = (size_t)kStateBytesPerCell * (size_t)s->N;
+  for (int b = 0; b < 2; ++b) {
+    CK(s, dalloc(s, &jp.in[b], bytes));
+    CK(s, dalloc(s, &jp.out[b], bytes));
+  }
+  CK(s, cudaStreamCreateWithFlags(&jp.s_in, cudaStreamNonBlocking));
+  CK(s, cudaStreamCreateWithFlags(&jp.s_out, cudaStreamNonBlocking));
+  for (int b = 0; b < 2; ++b)
+    for (cudaEvent_t* ev : {&jp.h2d_done[b], &jp.in_free[b], &jp.out_ready[b], &jp.out_free[b]})
+      CK(s, cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+  jp.ready = true;
+  return CORAL_OK;
+}
+
+// Enqueues job k of coral_step_jobs (see the header): copy in on s_in, load + validate +
+// steps + copy to the output staging buffer on the substrate's stream, copy out on s_out.
+int enqueue_job(coral_substrate* s, int k, const void* src, void* dst, int32_t n_steps, int64_t t0) {
+  JobPipe& jp = s->jobs;
+  const int b = k & 1;
+  const long long N = s->N;
+  const size_t bytes = (size_t)kStateBytesPerCell * (size_t)N;
+  if (k >= 2) CK(s, cudaStreamWaitEvent(jp.s_in, jp.in_free[b], 0));
+  CK(s, cudaMemcpyAsync(jp.in[b], src, bytes, cudaMemcpyHostToDevice, jp.s_in));
+  CK(s, cudaEventRecord(jp.h2d_done[b], jp.s_in));
+  CK(s, cudaStreamWaitEvent(s->stream, jp.h2d_done[b], 0));
+  {
+    const Planes& d = s->st[s->cur];
+    CK(s, cudaMemcpyAsync(d.E, jp.in[b], sizeof(float) * 6 * N, cudaMemcpyDeviceToDevice, s->stream));
+    CK(s, cudaMemcpyAsync(d.G, jp.in[b] + 24 * N, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s->stream));
+    CK(s, cudaMemcpyAsync(d.R, jp.in[b] + 28 * N, (size_t)N, cudaMemcpyDeviceToDevice, s->stream));
+    CK(s, cudaEventRecord(jp.in_free[b], s->stream));
+    CK(s, launch_validate_state(d.G, d.R, N, s->cap, s->status, s->stream));
+  }
+  s->t = t0;
+  for (int i = 0; i < n_steps; ++i) {
+    const int rc = enqueue_step(s, nullptr);
+    if (rc != CORAL_OK) return rc;
+  }
+  if (k >= 2) CK(s, cudaStreamWaitEvent(s->stream, jp.out_free[b], 0));
+  {
+    const Planes& d = s->st[s->cur];
+    CK(s, cudaMemcpyAsync(jp.out[b], d.E, sizeof(float) * 6 * N, cudaMemcpyDeviceToDevice, s->stream));
+    CK(s, cudaMemcpyAsync(jp.out[b] + 24 * N, d.G, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s->stream));
+    CK(s, cudaMemcpyAsync(jp.out[b] + 28 * N, d.R, (size_t)N, cudaMemcpyDeviceToDevice, s->stream));
+  }
+  CK(s, cudaEventRecord(jp.out_ready[b], s->stream));
+  CK(s, cudaStreamWaitEvent(jp.s_out, jp.out_ready[b], 0));
+  CK(s, cudaMemcpyAsync(dst, jp.out[b], bytes, cudaMemcpyDeviceToHost, jp.s_out));
+  CK(s, cudaEventRecord(jp.out_free[b], jp.s_out));
+  return CORAL_OK;
+}
+
+}  // namespace
+
+extern "C" int coral_step_jobs(coral_substrate* s, int32_t n_jobs, const void* const* host_in,
+                               void* const* host_out, int32_t n_steps, int64_t t0) {
+  int rc = step_preconditions(s, n_steps);
+  if (rc) return rc;
+  if (n_jobs < 0 || t0 < 0) return fail(s, CORAL_E_INVALID, "n_jobs and t0 must be >= 0");
+  if (n_jobs == 0) return CORAL_OK;
+  if (!host_in || !host_out) return fail(s, CORAL_E_INVALID, "NULL job buffer array");
+  for (int k = 0; k < n_jobs; ++k)
+    if (!host_in[k] || !host_out[k]) return fail(s, CORAL_E_INVALID, "NULL job buffer");
+  if ((rc = jobs_setup(s)) != CORAL_OK) return rc;
+  for (int k = 0; k < n_jobs && rc == CORAL_OK; ++k) rc = enqueue_job(s, k, host_in[k], host_out[k], n_steps, t0);
+  // the caller regains its buffers only when no copy is in flight, also after an error
+  cudaStreamSynchronize(s->jobs.s_in);
+  cudaStreamSynchronize(s->stream);
+  cudaStreamSynchronize(s->jobs.s_out);
+  if (rc != CORAL_OK) return rc;
+  return check_status(s);
 }
 
 extern "C" int coral_step_timed(coral_substrate* s, int32_t n_steps, float* step_ms, float* stage_ms) {

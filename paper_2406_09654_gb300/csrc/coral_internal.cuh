@@ -56,6 +56,9 @@ __host__ __device__ inline int bf16_blob_bytes(int H) {
   return (n + 127) & ~127;
 }
 
+// Packed state of one cell in host transfers: E, I, C0..C3 float32, G int32, R uint8.
+constexpr int kStateBytesPerCell = 6 * 4 + 4 + 1;
+
 struct Planes {     // the six sensor planes are contiguous: I = E + N, C = E + 2N
   float* E;
   float* I;

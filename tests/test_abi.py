@@ -60,6 +60,7 @@ def test_invalid_arguments_fail_before_any_device_work(lib):
         coral.Substrate(p, 8, 8, 4)
     assert e.value.code == coral.E_INVALID
     assert lib.coral_step(None, 1) == coral.E_INVALID
+    assert lib.coral_step_jobs(None, 1, None, None, 1, 0) == coral.E_INVALID
     assert b"NULL" in lib.coral_last_error(None)
 
 
