@@ -46,6 +46,7 @@ struct coral_substrate {
   int* status = nullptr;
   // radiation scratch
   int32_t* count = nullptr;
+  uint8_t* hitmask = nullptr;
   int32_t* blockcnt = nullptr;
   int32_t* blockoff = nullptr;
   int4* hits = nullptr;
@@ -234,11 +235,14 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
     ok = ok && dalloc(s, &s->part1, kMaxPartials) == cudaSuccess && dalloc(s, &s->part2, kMaxPartials) == cudaSuccess &&
          dalloc(s, &s->ring, kRing) == cudaSuccess && dalloc(s, &s->status, 4) == cudaSuccess;
     const int nblk = radiation_blocks(N);
-    ok = ok && dalloc(s, &s->count, genome_capacity) == cudaSuccess && dalloc(s, &s->blockcnt, nblk) == cudaSuccess &&
-         dalloc(s, &s->blockoff, nblk) == cudaSuccess && dalloc(s, &s->hits, genome_capacity) == cudaSuccess &&
+    // per-block counts of the hit passes (cells) and of the free-slot passes (slots)
+    const int nbc = std::max(nblk, (genome_capacity + 1023) / 1024);
+    ok = ok && dalloc(s, &s->count, genome_capacity) == cudaSuccess && dalloc(s, &s->blockcnt, nbc) == cudaSuccess &&
+         dalloc(s, &s->blockoff, nbc) == cudaSuccess && dalloc(s, &s->hits, genome_capacity) == cudaSuccess &&
          dalloc(s, &s->hitbits, genome_capacity) == cudaSuccess &&
          dalloc(s, &s->freelist, genome_capacity) == cudaSuccess &&
-         dalloc(s, &s->newslots, genome_capacity) == cudaSuccess && dalloc(s, &s->counters, 8) == cudaSuccess;
+         dalloc(s, &s->newslots, genome_capacity) == cudaSuccess && dalloc(s, &s->counters, 8) == cudaSuccess &&
+         dalloc(s, &s->hitmask, (size_t)nblk * radiation_threads()) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
       rc = fail(s, CORAL_E_OOM, "device allocation failed");
@@ -387,6 +391,7 @@ int enqueue_step(coral_substrate* s, cudaEvent_t* ev) {
     r.seed = s->p.seed;
     r.step = (uint32_t)s->t;
     r.count = s->count;
+    r.hitmask = s->hitmask;
     r.blockcnt = s->blockcnt;
     r.blockoff = s->blockoff;
     r.hits = s->hits;

@@ -246,9 +246,10 @@ struct RadiationArgs {
   unsigned long long seed;
   uint32_t step;
   // scratch
-  int32_t* count;             // [cap]
-  int32_t* blockcnt;          // [nblk]
-  int32_t* blockoff;          // [nblk]
+  int32_t* count;             // [cap]: 1 for slots that own a cell, else 0
+  uint8_t* hitmask;           // [nblk * kRadThreads]: hit bits of each thread's 8 cells
+  int32_t* blockcnt;          // [max(nblk, slot blocks)]: hits per block, then free slots per block
+  int32_t* blockoff;          // [max(nblk, slot blocks)]: hit offsets, then live slots per block
   int4* hits;                 // [max_hits] (cell, parent, partner or -1, flags)
   uint32_t* hitbits;          // [max_hits]
   int max_hits;
@@ -259,6 +260,7 @@ struct RadiationArgs {
 };
 cudaError_t launch_radiation(const RadiationArgs& r, cudaStream_t st);
 int radiation_blocks(long long N);
+int radiation_threads();   // threads per radiation block (one hit-mask byte each)
 
 struct SortArgs {
   const int32_t* keys_in;     // [N]

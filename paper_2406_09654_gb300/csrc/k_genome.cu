@@ -213,6 +213,7 @@ __device__ __forceinline__ int block_exscan(int v, int& total) {
 __global__ void __launch_bounds__(kRadThreads) k_rad_count(RadiationArgs r) {
   const long long base = (long long)blockIdx.x * kRadTile + (long long)threadIdx.x * kRadPerThread;
   int nh = 0, nm = 0, ng = 0;
+  uint32_t mask = 0;
   for (int i = 0; i < kRadPerThread; ++i) {
     const long long j = base + i;
     if (j >= r.N) break;
@@ -220,7 +221,9 @@ __global__ void __launch_bounds__(kRadThreads) k_rad_count(RadiationArgs r) {
     nh += h.hit;
     nm += h.mut;
     ng += h.merge;
+    mask |= (uint32_t)h.hit << i;
   }
+  r.hitmask[(long long)blockIdx.x * kRadThreads + threadIdx.x] = (uint8_t)mask;
   int tot;
   block_exscan(nh, tot);
   int tm, tg;
@@ -267,25 +270,61 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t* in, int32_t* out, 
   if (threadIdx.x == 0 && total) *total = carry;
 }
 
+// Writes the hits in cell order. The counting pass left each thread's hit bits in the mask, so
+// only hit cells (about p_mut + p_merge of them) draw their Philox numbers again here.
 __global__ void __launch_bounds__(kRadThreads) k_rad_emit(RadiationArgs r) {
   const long long base = (long long)blockIdx.x * kRadTile + (long long)threadIdx.x * kRadPerThread;
-  Hit hs[kRadPerThread];
-  int nh = 0;
-  for (int i = 0; i < kRadPerThread; ++i) {
-    const long long j = base + i;
-    hs[i] = j < r.N ? radiation_hit(r, j) : Hit{false, false, false, 0, -1, 0};
-    nh += hs[i].hit;
-  }
+  uint32_t mask = r.hitmask[(long long)blockIdx.x * kRadThreads + threadIdx.x];
   int tot;
-  int pos = r.blockoff[blockIdx.x] + block_exscan(nh, tot);
-  for (int i = 0; i < kRadPerThread; ++i) {
-    if (!hs[i].hit) continue;
+  int pos = r.blockoff[blockIdx.x] + block_exscan(__popc(mask), tot);
+  while (mask) {
+    const int i = __ffs(mask) - 1;
+    mask &= mask - 1;
+    const Hit h = radiation_hit(r, base + i);
     if (pos < r.max_hits) {
-      r.hits[pos] = make_int4((int)(base + i), hs[i].g, hs[i].merge ? hs[i].gp : -1,
-                              (hs[i].mut ? 1 : 0) | (hs[i].merge ? 2 : 0));
-      r.hitbits[pos] = hs[i].bits;
+      r.hits[pos] = make_int4((int)(base + i), h.g, h.merge ? h.gp : -1, (h.mut ? 1 : 0) | (h.merge ? 2 : 0));
+      r.hitbits[pos] = h.bits;
     }
     ++pos;
+  }
+}
+
+// Marks the slots that own at least one cell (flag[g] = 1). Each block collects the slots of
+// its contiguous range of cells in a shared bitmap (one shared-memory OR per distinct slot of a
+// warp's 32 cells), then writes one global flag per slot it saw: genomes occupy blobs, so a few
+// stores per block instead of one per cell on a handful of hot lines.
+constexpr int kLiveThreads = 256;
+constexpr int kLiveMaxWords = 2048;                 // bitmap of up to 65,536 slots
+__global__ void __launch_bounds__(kLiveThreads) k_live(const int32_t* G, long long N, int cap, int32_t* flag) {
+  __shared__ uint32_t bits[kLiveMaxWords];
+  const int words = (cap + 31) >> 5;
+  for (int i = threadIdx.x; i < words; i += kLiveThreads) bits[i] = 0;
+  __syncthreads();
+  const long long per = (N + gridDim.x - 1) / gridDim.x;
+  const long long j0 = (long long)blockIdx.x * per;
+  const long long j1 = j0 + per < N ? j0 + per : N;
+  for (long long b = j0; b < j1; b += kLiveThreads) {
+    const long long j = b + threadIdx.x;
+    const int g = j < j1 ? G[j] : -1;
+    const unsigned m = __match_any_sync(0xffffffffu, g);
+    if (g >= 0 && g < cap && (threadIdx.x & 31) == __ffs(m) - 1) atomicOr(&bits[g >> 5], 1u << (g & 31));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < words; i += kLiveThreads) {
+    uint32_t w = bits[i];
+    while (w) {
+      const int k = __ffs(w) - 1;
+      w &= w - 1;
+      flag[32 * i + k] = 1;
+    }
+  }
+}
+
+// Slots without cells fall back to one store per cell when the bitmap would not fit.
+__global__ void k_live_plain(const int32_t* G, long long N, int32_t* flag) {
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
+    const int g = G[j];
+    if (g >= 0) flag[g] = 1;
   }
 }
 
@@ -301,36 +340,58 @@ __global__ void k_hist(const int32_t* G, long long N, int32_t* count) {
   }
 }
 
-// Free slots (count 0) in increasing order; live count.
-__global__ void __launch_bounds__(1024) k_free(RadiationArgs r) {
-  __shared__ int wt[32];
-  __shared__ int carry, live;
-  if (threadIdx.x == 0) carry = live = 0;
-  __syncthreads();
+// Free slots (flag 0) in increasing order and the live count, in two passes over blocks of
+// 1024 consecutive slots: per-block counts, then each block's free slots compacted in order at
+// the offset of the blocks before it.
+constexpr int kFreeBlock = 1024;
+__global__ void __launch_bounds__(kFreeBlock) k_free_count(RadiationArgs r) {
+  __shared__ int wf[32], wl[32];
+  const int sl = blockIdx.x * kFreeBlock + threadIdx.x;
+  const int c = sl < r.g.capacity ? r.count[sl] : -1;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int s0 = 0; s0 < r.g.capacity; s0 += 1024) {
-    const int s = s0 + threadIdx.x;
-    const bool fr = s < r.g.capacity && r.count[s] == 0;
-    const bool lv = s < r.g.capacity && r.count[s] > 0;
-    const unsigned b = __ballot_sync(0xffffffffu, fr);
-    const int lv_w = __popc(__ballot_sync(0xffffffffu, lv));
-    if (lane == 0) wt[w] = __popc(b);
-    if (lane == 0 && lv_w) atomicAdd(&live, lv_w);
-    __syncthreads();
-    int before = 0, tot = 0;
-    for (int i = 0; i < 32; ++i) {
-      if (i < w) before += wt[i];
-      tot += wt[i];
-    }
-    if (fr) r.freelist[carry + before + __popc(b & ((1u << lane) - 1))] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += tot;
-    __syncthreads();
+  const int f = __popc(__ballot_sync(0xffffffffu, c == 0)), l = __popc(__ballot_sync(0xffffffffu, c > 0));
+  if (lane == 0) {
+    wf[w] = f;
+    wl[w] = l;
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    r.counters[1] = carry;
-    r.counters[5] = live;
+    int tf = 0, tl = 0;
+    for (int i = 0; i < 32; ++i) {
+      tf += wf[i];
+      tl += wl[i];
+    }
+    r.blockcnt[blockIdx.x] = tf;
+    r.blockoff[blockIdx.x] = tl;           // live slots of this block
   }
+}
+
+__global__ void __launch_bounds__(kFreeBlock) k_free_emit(RadiationArgs r) {
+  __shared__ int wf[32];
+  __shared__ int base;
+  const int sl = blockIdx.x * kFreeBlock + threadIdx.x;
+  const int c = sl < r.g.capacity ? r.count[sl] : -1;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned b = __ballot_sync(0xffffffffu, c == 0);
+  if (lane == 0) wf[w] = __popc(b);
+  if (threadIdx.x == 0) {
+    int off = 0;
+    for (int i = 0; i < (int)blockIdx.x; ++i) off += r.blockcnt[i];
+    base = off;
+    if (blockIdx.x == 0) {                 // totals: free slots and live slots
+      int tf = 0, tl = 0;
+      for (int i = 0; i < (int)gridDim.x; ++i) {
+        tf += r.blockcnt[i];
+        tl += r.blockoff[i];
+      }
+      r.counters[1] = tf;
+      r.counters[5] = tl;
+    }
+  }
+  __syncthreads();
+  int before = base;
+  for (int i = 0; i < w; ++i) before += wf[i];
+  if (c == 0) r.freelist[before + __popc(b & ((1u << lane) - 1))] = sl;
 }
 
 __global__ void __launch_bounds__(128) k_rad_assign(RadiationArgs r) {
@@ -468,6 +529,7 @@ cudaError_t launch_genome_distances(const float* genes, const int32_t* slots, in
 }
 
 int radiation_blocks(long long N) { return (int)((N + kRadTile - 1) / kRadTile); }
+int radiation_threads() { return kRadThreads; }
 int bucket_blocks(long long N) { return (int)((N + kSortTile - 1) / kSortTile); }
 
 cudaError_t launch_cppn_generate(const GenomeArgs& g, const int32_t* slots, const int* n_dev, int n_host,
@@ -505,11 +567,20 @@ cudaError_t launch_radiation(const RadiationArgs& r, cudaStream_t st) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(r.count, 0, sizeof(int32_t) * r.g.capacity, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(r.counters, 0, sizeof(int) * 8, st)) != cudaSuccess) return e;
-  k_hist<<<1024, 256, 0, st>>>(r.G, r.N, r.count);
+  if (r.g.capacity <= 32 * kLiveMaxWords)
+    k_live<<<1024, kLiveThreads, 0, st>>>(r.G, r.N, r.g.capacity, r.count);
+  else
+    k_live_plain<<<1024, 256, 0, st>>>(r.G, r.N, r.count);
   k_rad_count<<<nblk, kRadThreads, 0, st>>>(r);
   k_scan<<<1, 1024, 0, st>>>(r.blockcnt, r.blockoff, nblk, &r.counters[0]);
   k_rad_emit<<<nblk, kRadThreads, 0, st>>>(r);
-  k_free<<<1, 1024, 0, st>>>(r);
+  {
+    // blockcnt / blockoff are free again once the hits are emitted; the slot passes reuse them
+    RadiationArgs f = r;
+    const int fblk = (r.g.capacity + kFreeBlock - 1) / kFreeBlock;
+    k_free_count<<<fblk, kFreeBlock, 0, st>>>(f);
+    k_free_emit<<<fblk, kFreeBlock, 0, st>>>(f);
+  }
   k_rad_assign<<<64, 128, 0, st>>>(r);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_cppn_generate(r.g, r.newslots, &r.counters[2], 0, st)) != cudaSuccess) return e;
