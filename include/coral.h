@@ -191,7 +191,8 @@ int coral_read_channels(coral_substrate* s, uint32_t channel_mask, void* dst, si
  * of device staging buffers (allocated at the first call, 4 x 29 bytes per cell, kept until
  * destroy); page-locked host buffers let the copies overlap. Returns after every result is in
  * host memory; the substrate's own state is then the last job's result and its step counter
- * t0 + n_steps. Errors: E_INVALID for bad arguments or an invalid G/R in any input (reported
+ * t0 + n_steps. The genome table is the substrate's: a radiation event inside one job changes
+ * it for the jobs after it. Errors: E_INVALID for bad arguments or an invalid G/R in any input (reported
  * after all jobs ran), E_OOM, E_CUDA. The paper has no counterpart: this is the library's
  * host-to-host stepping path, used for the end-to-end throughput.
  */
