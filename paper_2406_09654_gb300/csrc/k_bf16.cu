@@ -287,6 +287,9 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       }
       if (gs < 0) break;
       if (staged != gs) {                             // stage this genome's BF16 blob
+        // in a later round of a tile, slower threads may still be reading the previous
+        // genome's b2 (no barrier since): wait for them (rare: tiles with several genomes)
+        if (!first_round) __syncthreads();
         const uint4* src = reinterpret_cast<const uint4*>(a.nets16 + (long long)gs * a.blob_bytes);
         const int n16 = a.blob_bytes >> 4;             // <= 648 = 6 x 108 per thread slot
 #pragma unroll
