@@ -315,7 +315,9 @@ def run_coral(a, rank, world_size, local):
     value = N * a.steps * world_size / total_s
     M = int(w.physics.get("radiation_every", 0))
     n_rad = sum(1 for t in range(t_first, t_first + a.steps) if M and (t + 1) % M == 0)
-    launches = 3 * a.steps + 8 * n_rad
+    # per step: pass 1, pass 2, totals; per radiation event: liveness, hit count, scan, hit
+    # emit, free-slot count and emit, slot assignment, CPPN weights, BF16 packing
+    launches = 3 * a.steps + 9 * n_rad
 
     # dominant kernel: pass 1 (the network)
     p1_ms = float(np.mean(stage_ms[:, 0]))
