@@ -804,7 +804,7 @@ int batch_configure(coral_batch* b) {
     }
     cudaGraph_t graph = nullptr;
     BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = launch_pass1_bf16_batch(t, p, b->grid1, b->stream);
+    cudaError_t e = launch_pass1_bf16_batch(t, p, b->grid1, b->worlds[0]->p.hidden, b->stream);
     if (e == cudaSuccess) e = launch_pass2_batch(t, p, b->grid2, b->stream);
     if (e == cudaSuccess) e = launch_stats_batch(t, b->stream);
     const cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);

@@ -205,7 +205,7 @@ __device__ __forceinline__ void copy_args_to_shared(StepArgs* dst, const StepArg
 }
 
 cudaError_t prepare_pass1_bf16_batch();   // kernel attributes, once before any capture
-cudaError_t launch_pass1_bf16_batch(const BatchTable& b, int parity, int grid, cudaStream_t st);
+cudaError_t launch_pass1_bf16_batch(const BatchTable& b, int parity, int grid, int hidden, cudaStream_t st);
 cudaError_t launch_pass2_batch(const BatchTable& b, int parity, int grid, cudaStream_t st);
 cudaError_t launch_stats_batch(const BatchTable& b, cudaStream_t st);
 int pass1_fp32_grid(int sms);

@@ -94,6 +94,9 @@ __device__ __forceinline__ void issue_halo(const StepArgs& a, int x0, int y0, ui
 
 // One CTA's share of pass 1 for one world: CTA `cta` of `ncta` takes a contiguous run of tiles;
 // its partial sums go to a.part1[cta]. tmap: TMA descriptor (use_tma != 0) or unused.
+// kH: the hidden size (0 = one layer), a compile-time constant so that the per-chunk loops and
+// the layer-2 branch are resolved by the compiler; one instantiation per supported size.
+template <int kH>
 __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtensorMap* tmap, const int use_tma,
                                                 const int cta, const int ncta) {
   extern __shared__ uint8_t smem_raw[];
@@ -112,8 +115,8 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int lx = tid % kTileW, ly = tid / kTileW;     // this thread's cell within a tile
   const int W = a.W, Hh = a.H;
-  const int H = a.hidden;
-  const int N1 = H ? H : 16;
+  constexpr int H = kH;
+  constexpr int N1 = H ? H : 16;
   const uint32_t rec_s = base_s + kOffRec;
   const uint32_t w_s = base_s + kOffW;
   const uint32_t a_s = base_s + kOffA;
@@ -347,7 +350,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       if (!tc::mbar_wait(mbar, phase, kWaitCycles)) bad = true;
       phase ^= 1;
       tc::tc_fence_after();
-      if (H == 0) {
+      if constexpr (H == 0) {
         float v[16];
         tc::tmem_ld16(t_lane, v);
         tc::tmem_wait_ld();
@@ -359,6 +362,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
         }
       } else {
         // hidden layer: tanh, BF16, written over this row of the (consumed) input tile
+#pragma unroll
         for (int c16 = 0; c16 < N1 / 16; ++c16) {
           float v[16];
           tc::tmem_ld16(t_lane + c16 * 16, v);
@@ -380,6 +384,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
         if (tid == 0) {
           tc::tc_fence_after();
           const uint64_t ad = tc::sdesc_sw128(a_s), bd = tc::sdesc_sw128(w_s + bf16_w2_off(H));
+#pragma unroll
           for (int k = 0; k < N1 / 16; ++k) tc::mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc2, k > 0);
           tc::mma_commit(mbar);
         }
@@ -435,18 +440,20 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   }
 }
 
+template <int kH>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     k_pass1_bf16(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tmap, const int use_tma) {
-  pass1_bf16_body(a, &tmap, use_tma, blockIdx.x, gridDim.x);
+  pass1_bf16_body<kH>(a, &tmap, use_tma, blockIdx.x, gridDim.x);
 }
 
+template <int kH>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16_batch(const __grid_constant__ BatchTable bt,
                                                                           const int parity) {
   __shared__ StepArgs sa;
   const int w = bt.cta_world1[blockIdx.x];
   copy_args_to_shared(&sa, &bt.args[parity * bt.n + w]);
   __syncthreads();
-  pass1_bf16_body(sa, nullptr, 0, blockIdx.x - bt.world_first1[w], bt.world_ctas1[w]);
+  pass1_bf16_body<kH>(sa, nullptr, 0, blockIdx.x - bt.world_first1[w], bt.world_ctas1[w]);
 }
 
 // A wait that must run out: nothing arrives on the barrier. Same bounded wait, error report
@@ -486,6 +493,16 @@ cudaError_t launch_selftest_wait(long long max_cycles, int* status, cudaStream_t
 
 size_t pass1_bf16_smem() { return kSmemBytes; }
 
+namespace {
+// the kernel instantiations, indexed by hidden size / 16 (0, 16, 32, 48, 64)
+using P1Fn = void (*)(StepArgs, CUtensorMap, int);
+using P1BFn = void (*)(BatchTable, int);
+const P1Fn kP1[5] = {k_pass1_bf16<0>, k_pass1_bf16<16>, k_pass1_bf16<32>, k_pass1_bf16<48>, k_pass1_bf16<64>};
+const P1BFn kP1B[5] = {k_pass1_bf16_batch<0>, k_pass1_bf16_batch<16>, k_pass1_bf16_batch<32>,
+                       k_pass1_bf16_batch<48>, k_pass1_bf16_batch<64>};
+int hidden_index(int hidden) { return (hidden >= 0 && hidden <= 64 && hidden % 16 == 0) ? hidden / 16 : -1; }
+}  // namespace
+
 long long pass1_bf16_tiles(int W, int H) {
   return (long long)((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH);
 }
@@ -495,30 +512,34 @@ int pass1_bf16_grid(int sms) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   if (major != 10) return 0;                                  // tcgen05 needs the sm_100 family
-  if (cudaFuncSetAttribute(k_pass1_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
-      cudaFuncSetAttribute(k_pass1_bf16, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pass1_bf16, kThreads, kSmemBytes) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
+  int per_sm = kCtasPerSm, max_regs = 0, static_smem = 0;
+  for (int k = 0; k < 5; ++k) {
+    const void* fn = reinterpret_cast<const void*>(kP1[k]);
+    int n = 0;
+    cudaFuncAttributes fa;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kThreads, kSmemBytes) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    if (n < per_sm) per_sm = n;
+    if (fa.numRegs > max_regs) max_regs = fa.numRegs;
+    if ((int)fa.sharedSizeBytes > static_smem) static_smem = (int)fa.sharedSizeBytes;
   }
   // Residency is bounded by TMEM (kCtasPerSm x 64 of 512 columns) and by the register and
-  // shared-memory budgets the kernel was compiled for, which allow kCtasPerSm.
+  // shared-memory budgets the kernels were compiled for, which allow kCtasPerSm (the occupancy
+  // query does not count the shared-memory carveout the launch asks for).
   if (per_sm < kCtasPerSm) {
     int smem_sm = 0, regs_sm = 0;
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_pass1_bf16) == cudaSuccess) {
-      const int by_smem = smem_sm / (kSmemBytes + (int)fa.sharedSizeBytes + 1024);
-      const int by_regs = regs_sm / (fa.numRegs * kThreads);
-      int est = by_smem < by_regs ? by_smem : by_regs;
-      if (est > per_sm) per_sm = est;
-    }
+    const int by_smem = smem_sm / (kSmemBytes + static_smem + 1024);
+    const int by_regs = max_regs > 0 ? regs_sm / (max_regs * kThreads) : 0;
+    const int est = by_smem < by_regs ? by_smem : by_regs;
+    if (est > per_sm) per_sm = est;
   }
   if (per_sm > kCtasPerSm) per_sm = kCtasPerSm;
   if (per_sm < 1) return 0;
@@ -527,25 +548,32 @@ int pass1_bf16_grid(int sms) {
 }
 
 cudaError_t prepare_pass1_bf16_batch() {
-  cudaError_t e = cudaFuncSetAttribute(k_pass1_bf16_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_pass1_bf16_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-  return e;
+  for (int k = 0; k < 5; ++k) {
+    const void* fn = reinterpret_cast<const void*>(kP1B[k]);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
-cudaError_t launch_pass1_bf16_batch(const BatchTable& b, int parity, int grid, cudaStream_t st) {
-  k_pass1_bf16_batch<<<grid, kThreads, kSmemBytes, st>>>(b, parity);
+cudaError_t launch_pass1_bf16_batch(const BatchTable& b, int parity, int grid, int hidden, cudaStream_t st) {
+  const int k = hidden_index(hidden);
+  if (k < 0) return cudaErrorInvalidValue;
+  kP1B[k]<<<grid, kThreads, kSmemBytes, st>>>(b, parity);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pass1_bf16(const StepArgs& a, const CUtensorMap* tmap, cudaStream_t st, int grid) {
+  const int k = hidden_index(a.hidden);
+  if (k < 0) return cudaErrorInvalidValue;
   CUtensorMap m;
   if (tmap)
     m = *tmap;
   else
     memset(&m, 0, sizeof(m));
-  k_pass1_bf16<<<grid, kThreads, kSmemBytes, st>>>(a, m, tmap ? 1 : 0);
+  kP1[k]<<<grid, kThreads, kSmemBytes, st>>>(a, m, tmap ? 1 : 0);
   return cudaGetLastError();
 }
 
