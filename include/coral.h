@@ -122,8 +122,10 @@ int coral_substrate_destroy(coral_substrate* s);
  * Copies a full state in: E, I [N], C [4][N] float32; G [N] int32 (each in
  * [0, genome_capacity)); R [N] uint8 (each in 0..3). Any of the five pointers may be NULL
  * to leave that channel unchanged. Values of G and R are checked on the device; a bad
- * value is reported by the next synchronising call as E_INVALID. Also resets the step
- * counter to 0 unless coral_set_step is called afterwards.
+ * value is reported by the next synchronising call as E_INVALID. Steps enqueued before that
+ * stay within the library's buffers: a cell whose G is out of range runs slot 0's net and is
+ * never a parent or partner at radiation; an R above 3 gives an unspecified rotation. Also resets the step counter to 0 unless coral_set_step is
+ * called afterwards.
  */
 int coral_state_load(coral_substrate* s, const float* E, const float* I, const float* C,
                      const int32_t* G, const uint8_t* R, int src_on_device);

@@ -127,6 +127,7 @@ StepArgs step_args(const coral_substrate* s) {
   a.max_mma_genomes = s->p.max_mma_genomes;
   a.status = s->status;
   a.day_period = s->p.day_period;
+  a.capacity = s->cap;
   a.step_dev = nullptr;
   return a;
 }

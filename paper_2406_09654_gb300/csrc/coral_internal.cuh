@@ -102,6 +102,7 @@ struct __align__(8) StepArgs {
   int max_mma_genomes;
   int* status;
   int day_period;
+  int capacity;     // genome slots: a GenomeIndex outside [0, capacity) acts as "no genome"
   const long long* step_dev;   // batched stepping: this world's step index on the device (day/night
                                // is taken from it); NULL: use is_day
 };

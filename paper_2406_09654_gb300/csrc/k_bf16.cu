@@ -293,7 +293,10 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
         // in a later round of a tile, slower threads may still be reading the previous
         // genome's b2 (no barrier since): wait for them (rare: tiles with several genomes)
         if (!first_round) __syncthreads();
-        const uint4* src = reinterpret_cast<const uint4*>(a.nets16 + (long long)gs * a.blob_bytes);
+        // an out-of-range GenomeIndex (loaded, reported as invalid, not yet read back) runs
+        // slot 0's net instead of reading outside the genome table
+        const int gsafe = (unsigned)gs < (unsigned)a.capacity ? gs : 0;
+        const uint4* src = reinterpret_cast<const uint4*>(a.nets16 + (long long)gsafe * a.blob_bytes);
         const int n16 = a.blob_bytes >> 4;             // <= 648 = 6 x 108 per thread slot
 #pragma unroll
         for (int half = 0; half < 2; ++half) {

@@ -167,6 +167,8 @@ struct Hit {
 __device__ __forceinline__ Hit radiation_hit(const RadiationArgs& r, long long j) {
   Hit h = {false, false, false, 0, -1, 0};
   const uint32_t cell = (uint32_t)j;
+  const uint32_t cap = (uint32_t)r.g.capacity;
+  if ((uint32_t)r.G[j] >= cap) return h;              // invalid GenomeIndex: never a parent
   if (r.thr_mut) h.mut = draw(cell, r.step, 0, 0, r.world, r.seed).x < r.thr_mut;
   if (r.thr_merge) {
     const uint4 w = draw(cell, r.step, 1, 0, r.world, r.seed);
@@ -176,7 +178,7 @@ __device__ __forceinline__ Hit radiation_hit(const RadiationArgs& r, long long j
       octant_offset(2 * (int)(w.y & 3u), dx, dy);     // von Neumann N, E, S, W
       const long long n = (long long)wrap(y + dy, r.H) * r.W + wrap(x + dx, r.W);
       const int32_t gp = r.G[n];
-      if (gp != r.G[j]) {
+      if (gp != r.G[j] && (uint32_t)gp < cap) {
         h.merge = true;
         h.gp = gp;
         h.bits = w.z;
@@ -321,14 +323,14 @@ __global__ void __launch_bounds__(kLiveThreads) k_live(const int32_t* G, long lo
 }
 
 // Slots without cells fall back to one store per cell when the bitmap would not fit.
-__global__ void k_live_plain(const int32_t* G, long long N, int32_t* flag) {
+__global__ void k_live_plain(const int32_t* G, long long N, int cap, int32_t* flag) {
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (long long)gridDim.x * blockDim.x) {
     const int g = G[j];
-    if (g >= 0) flag[g] = 1;
+    if (g >= 0 && g < cap) flag[g] = 1;
   }
 }
 
-__global__ void k_hist(const int32_t* G, long long N, int32_t* count) {
+__global__ void k_hist(const int32_t* G, long long N, int cap, int32_t* count) {
   const int lane = threadIdx.x & 31;
   const long long wbase = ((long long)blockIdx.x * blockDim.x + threadIdx.x) - lane;
   const long long wstride = (long long)gridDim.x * blockDim.x;
@@ -336,7 +338,7 @@ __global__ void k_hist(const int32_t* G, long long N, int32_t* count) {
     const long long j = b + lane;
     const int g = j < N ? G[j] : -1;
     const unsigned m = __match_any_sync(0xffffffffu, g);
-    if (g >= 0 && lane == __ffs(m) - 1) atomicAdd(&count[g], __popc(m));
+    if (g >= 0 && g < cap && lane == __ffs(m) - 1) atomicAdd(&count[g], __popc(m));
   }
 }
 
@@ -570,7 +572,7 @@ cudaError_t launch_radiation(const RadiationArgs& r, cudaStream_t st) {
   if (r.g.capacity <= 32 * kLiveMaxWords)
     k_live<<<1024, kLiveThreads, 0, st>>>(r.G, r.N, r.g.capacity, r.count);
   else
-    k_live_plain<<<1024, 256, 0, st>>>(r.G, r.N, r.count);
+    k_live_plain<<<1024, 256, 0, st>>>(r.G, r.N, r.g.capacity, r.count);
   k_rad_count<<<nblk, kRadThreads, 0, st>>>(r);
   k_scan<<<1, 1024, 0, st>>>(r.blockcnt, r.blockoff, nblk, &r.counters[0]);
   k_rad_emit<<<nblk, kRadThreads, 0, st>>>(r);
@@ -591,7 +593,7 @@ cudaError_t launch_bucket(const SortArgs& a, cudaStream_t st) {
   const int nblk = bucket_blocks(a.N);
   cudaError_t e;
   if ((e = cudaMemsetAsync(a.count, 0, sizeof(int32_t) * a.capacity, st)) != cudaSuccess) return e;
-  k_hist<<<1024, 256, 0, st>>>(a.keys_in, a.N, a.count);
+  k_hist<<<1024, 256, 0, st>>>(a.keys_in, a.N, a.capacity, a.count);
   int passes = 1;
   while (passes < 4 && (1LL << (8 * passes)) < (long long)a.capacity) ++passes;
   const int32_t* kin = a.keys_in;

@@ -73,7 +73,9 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1_fp32(const StepArgs a) {
         const long long n = (long long)wrap(y + dy, H) * W + wrap(x + dx, W);
         load6(a.cur, n, N, in + 6 * p);
       }
-      const float* net = a.nets32 + (long long)a.cur.G[j] * a.net_stride;
+      const int gj = a.cur.G[j];
+      // an out-of-range GenomeIndex (loaded, reported as invalid) runs slot 0's net
+      const float* net = a.nets32 + (long long)((unsigned)gj < (unsigned)a.capacity ? gj : 0) * a.net_stride;
       float act[kOut], zo[kOut];
       if (a.hidden == 0) {
 #pragma unroll
