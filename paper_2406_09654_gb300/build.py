@@ -6,6 +6,7 @@ x86_64 and aarch64).
 """
 from __future__ import annotations
 
+import fcntl
 import os
 import shutil
 import subprocess
@@ -42,8 +43,19 @@ def _stale(objs, lib):
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link; returns the library path. Skips work when nothing changed."""
+    """Compile and link; returns the library path. Skips work when nothing changed. Safe to
+    call from several processes at once (one rank per GPU): they take turns on a file lock,
+    and the later ones find the library up to date."""
     os.makedirs(LIBDIR, exist_ok=True)
+    with open(os.path.join(LIBDIR, ".build.lock"), "w") as lock:
+        fcntl.flock(lock, fcntl.LOCK_EX)
+        try:
+            return _build_locked(force, verbose)
+        finally:
+            fcntl.flock(lock, fcntl.LOCK_UN)
+
+
+def _build_locked(force: bool, verbose: bool) -> str:
     srcs = sources()
     objs = [os.path.join(LIBDIR, os.path.basename(s)[:-3] + ".o") for s in srcs]
     if not force and not _stale(objs, LIB):
