@@ -57,6 +57,7 @@ def parse():
     ap.add_argument("--workload", default="cfg3", choices=list(WORKLOADS))
     ap.add_argument("--fp32-steps", type=int, default=12, help="steps of the FP32 comparison run")
     ap.add_argument("--e2e-steps", type=int, default=12)
+    ap.add_argument("--bucket-reps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batched-steps", type=int, default=10, help="steps of the 256-world batch (0 = skip)")
@@ -379,6 +380,23 @@ def run_coral(a, rank, world_size, local):
         el = max_over_ranks(time.perf_counter() - t0, world_size)
         e2e = {"value": N * a.e2e_steps * world_size / el, "unit": "cell-updates/s",
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    # bucketing (stable counting sort of the cells by GenomeIndex) of the final state, device
+    # time of the sort kernels on the substrate's stream (the call then synchronises)
+    bucket = None
+    if a.bucket_reps > 0:
+        sub.read_perm_only()                                    # scratch allocation, first use
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(a.bucket_reps):
+            sub.read_perm_only()
+        b1.record(stream)
+        torch.cuda.synchronize()
+        ms = b0.elapsed_time(b1) / a.bucket_reps
+        gbs = 8 * N / (ms / 1e3) / 1e9
+        bucket = {"keys": N, "capacity": w.capacity, "ms": ms, "keys_per_s": N / (ms / 1e3),
+                  "hbm": {"achieved": gbs, "peak": measured_peaks()[0], "unit": "GB/s",
+                          "frac": gbs / measured_peaks()[0], "algorithmic_bytes_per_key": 8,
+                          "note": "4 B key read + 4 B permutation index written per cell"}}
     sub.close()
     batched = served = None
     if path == "bf16" and a.batched_steps > 0:
@@ -408,6 +426,7 @@ def run_coral(a, rank, world_size, local):
         "speedup_vs_fp32_plain": (value / world_size / fp32) if fp32 else None,
         "clocks": {"sm_mhz": ck.get("sm_mhz"), "sm_max_mhz": ck.get("sm_max_mhz"), "reasons": ck.get("reasons", [])},
         "e2e": e2e,
+        "bucket": bucket,
         "gpu_launches": launches,
         "batched_cfg4": batched,
         "serving_cfg5": served,

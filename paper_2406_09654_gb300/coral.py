@@ -235,6 +235,10 @@ class Substrate:
     def step(self, n=1):
         _check(lib().coral_step(self.h, int(n)), self.h)
 
+    def read_perm_only(self):
+        """Runs the bucketing sort (coral_read_perm) without copying its results out."""
+        _check(lib().coral_read_perm(self.h, None, None), self.h)
+
     def step_jobs(self, host_in, host_out, n_steps=1, t0=0):
         """Host-to-host stepping of independent states (coral_step_jobs): host_in / host_out
         are equal-length lists of packed-state buffers (29 bytes per cell, CH_ALL order; numpy

@@ -576,7 +576,7 @@ int coral_read_perm(coral_substrate* s, int32_t* dst_counts, int32_t* dst_perm) 
   const long long N = s->N;
   const int nblk = bucket_blocks(N);
   if (!s->sort_buf) {
-    const size_t words = 5 * (size_t)N + 256 * (size_t)nblk + (size_t)s->cap + 64;
+    const size_t words = 5 * (size_t)N + 256 * (size_t)nblk + (size_t)s->cap + 256 + 64;
     CK(s, dalloc(s, &s->sort_buf, words));
   }
   SortArgs a = {};
@@ -590,6 +590,7 @@ int coral_read_perm(coral_substrate* s, int32_t* dst_counts, int32_t* dst_perm) 
   a.perm = a.v1 + N;
   a.hist = a.perm + N;
   a.count = a.hist + 256 * (size_t)nblk;
+  a.totals = a.count + s->cap;
   CK(s, launch_bucket(a, s->stream));
   if (dst_counts) CK(s, cudaMemcpyAsync(dst_counts, a.count, sizeof(int32_t) * s->cap, cudaMemcpyDeviceToHost, s->stream));
   if (dst_perm) CK(s, cudaMemcpyAsync(dst_perm, a.perm, sizeof(int32_t) * N, cudaMemcpyDeviceToHost, s->stream));

@@ -272,6 +272,7 @@ struct SortArgs {
   int32_t* k0; int32_t* v0;   // ping-pong scratch [N]
   int32_t* k1; int32_t* v1;
   int32_t* hist;              // [256 * nblk]
+  int32_t* totals;            // [256]: keys per digit value of the current pass
 };
 cudaError_t launch_bucket(const SortArgs& a, cudaStream_t st);
 int bucket_blocks(long long N);

@@ -330,18 +330,6 @@ __global__ void k_live_plain(const int32_t* G, long long N, int cap, int32_t* fl
   }
 }
 
-__global__ void k_hist(const int32_t* G, long long N, int cap, int32_t* count) {
-  const int lane = threadIdx.x & 31;
-  const long long wbase = ((long long)blockIdx.x * blockDim.x + threadIdx.x) - lane;
-  const long long wstride = (long long)gridDim.x * blockDim.x;
-  for (long long b = wbase; b < N; b += wstride) {
-    const long long j = b + lane;
-    const int g = j < N ? G[j] : -1;
-    const unsigned m = __match_any_sync(0xffffffffu, g);
-    if (g >= 0 && g < cap && lane == __ffs(m) - 1) atomicAdd(&count[g], __popc(m));
-  }
-}
-
 // Free slots (flag 0) in increasing order and the live count, in two passes over blocks of
 // 1024 consecutive slots: per-block counts, then each block's free slots compacted in order at
 // the offset of the blocks before it.
@@ -465,10 +453,80 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_hist(const int32_t* keys,
   const long long base = (long long)blockIdx.x * kSortTile;
   for (int i = threadIdx.x; i < kSortTile; i += kSortThreads) {
     const long long j = base + i;
-    if (j < N) atomicAdd(&h[(keys[j] >> shift) & 255], 1);
+    const int d = j < N ? (keys[j] >> shift) & 255 : 256;
+    // one shared-memory add per distinct digit of the warp (genomes come in runs)
+    const unsigned m = __match_any_sync(0xffffffffu, d);
+    if (d < 256 && (threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&h[d], __popc(m));
   }
   __syncthreads();
   hist[(long long)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
+}
+
+// Keys per digit value: block d sums row d of the [256][nblk] block histograms.
+__global__ void __launch_bounds__(256) k_digit_totals(const int32_t* hist, int nblk, int32_t* totals) {
+  __shared__ int ws[8];
+  int v = 0;
+  for (int b = threadIdx.x; b < nblk; b += 256) v += hist[(long long)blockIdx.x * nblk + b];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int i = 0; i < 8; ++i) t += ws[i];
+    totals[blockIdx.x] = t;
+  }
+}
+
+// Exclusive scan of the histograms in digit-major order, one block per digit value: row d
+// starts at the keys of smaller digits and runs over the blocks in order (in place).
+__global__ void __launch_bounds__(1024) k_digit_scan(int32_t* hist, int nblk, const int32_t* totals) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) {
+    int base = 0;
+    for (int d = 0; d < (int)blockIdx.x; ++d) base += totals[d];
+    carry = base;
+  }
+  __syncthreads();
+  int32_t* row = hist + (long long)blockIdx.x * nblk;
+  for (int c0 = 0; c0 < nblk; c0 += 1024) {
+    const int b = c0 + threadIdx.x;
+    const int v = b < nblk ? row[b] : 0;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    int before = carry, tot = 0;
+    for (int i = 0; i < 32; ++i) {
+      if (i < w) before += wsum[i];
+      tot += wsum[i];
+    }
+    if (b < nblk) row[b] = before + inc - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+}
+
+// Keys per slot from the sorted keys: each block takes a contiguous chunk; a run of equal keys
+// inside it adds (last - c0 + 1) at its last element and -(first - c0) at its first, so each
+// slot receives the total length of its runs with two atomics per run and chunk.
+__global__ void __launch_bounds__(kSortThreads) k_count_runs(const int32_t* sk, long long N, int cap,
+                                                           int32_t* count) {
+  const long long c0 = (long long)blockIdx.x * kSortTile;
+  const long long c1 = c0 + kSortTile < N ? c0 + kSortTile : N;
+  for (long long i = c0 + threadIdx.x; i < c1; i += kSortThreads) {
+    const int k = sk[i];
+    if (k < 0 || k >= cap) continue;
+    if (i == c0 || sk[i - 1] != k) atomicAdd(&count[k], -(int)(i - c0));
+    if (i == c1 - 1 || sk[i + 1] != k) atomicAdd(&count[k], (int)(i - c0 + 1));
+  }
 }
 
 __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const int32_t* kin, const int32_t* vin,
@@ -593,7 +651,6 @@ cudaError_t launch_bucket(const SortArgs& a, cudaStream_t st) {
   const int nblk = bucket_blocks(a.N);
   cudaError_t e;
   if ((e = cudaMemsetAsync(a.count, 0, sizeof(int32_t) * a.capacity, st)) != cudaSuccess) return e;
-  k_hist<<<1024, 256, 0, st>>>(a.keys_in, a.N, a.capacity, a.count);
   int passes = 1;
   while (passes < 4 && (1LL << (8 * passes)) < (long long)a.capacity) ++passes;
   const int32_t* kin = a.keys_in;
@@ -602,11 +659,13 @@ cudaError_t launch_bucket(const SortArgs& a, cudaStream_t st) {
     int32_t* kout = (p & 1) ? a.k1 : a.k0;
     int32_t* vout = (p + 1 == passes) ? a.perm : ((p & 1) ? a.v1 : a.v0);
     k_sort_hist<<<nblk, kSortThreads, 0, st>>>(kin, a.N, 8 * p, a.hist, nblk);
-    k_scan<<<1, 1024, 0, st>>>(a.hist, a.hist, 256LL * nblk, nullptr);
+    k_digit_totals<<<256, 256, 0, st>>>(a.hist, nblk, a.totals);
+    k_digit_scan<<<256, 1024, 0, st>>>(a.hist, nblk, a.totals);
     k_sort_scatter<<<nblk, kSortThreads, 0, st>>>(kin, vin, kout, vout, a.N, 8 * p, a.hist, nblk);
     kin = kout;
     vin = vout;
   }
+  k_count_runs<<<nblk, kSortThreads, 0, st>>>(kin, a.N, a.capacity, a.count);   // kin: sorted keys
   return cudaGetLastError();
 }
 

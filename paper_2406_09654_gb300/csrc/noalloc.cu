@@ -17,8 +17,9 @@ namespace {
 constexpr long long kNoAllocMaxCells = 1LL << 20;          // 1,048,576 cells (e.g. 1024 x 1024)
 constexpr int kNoAllocMaxCapacity = 1 << 16;               // genome ids below 65,536: two digit passes
 constexpr long long kNoAllocMaxBlocks = kNoAllocMaxCells / 4096;
-// three [cells] int32 ping-pong arrays + the [256][blocks] digit histograms: 12.3 MiB
-constexpr long long kNoAllocWords = 3 * kNoAllocMaxCells + 256 * kNoAllocMaxBlocks;
+// three [cells] int32 ping-pong arrays + the [256][blocks] digit histograms + 256 digit
+// totals: 12.3 MiB
+constexpr long long kNoAllocWords = 3 * kNoAllocMaxCells + 256 * kNoAllocMaxBlocks + 256;
 
 __device__ __align__(256) int32_t g_bucket_scratch[kNoAllocWords];
 
@@ -80,6 +81,7 @@ extern "C" int coral_bucket_noalloc(const int32_t* G, int64_t n_cells, int32_t c
   a.k1 = scratch + 2 * n_cells;         // never read; counts are zeroed by the launch itself
   a.v1 = nullptr;                       // unused: at most two digit passes
   a.hist = scratch + 3 * kNoAllocMaxCells;
+  a.totals = a.hist + 256 * kNoAllocMaxBlocks;
   e = launch_bucket(a, reinterpret_cast<cudaStream_t>(cuda_stream));
   if (e != cudaSuccess) return noalloc_fail(CORAL_E_CUDA, std::string("launch: ") + cudaGetErrorString(e));
   return CORAL_OK;
