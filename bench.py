@@ -166,22 +166,35 @@ def measured_peaks():
     return 6800.0, 1900.0, 2070.0, "fallback"
 
 
-def kernel_source_hash():
+# translation unit of each profiled kernel; every header and the build flags count for all
+KERNEL_UNITS = {"pass1_bf16": "k_bf16.cu", "pass1_fp32": "k_step.cu", "pass2": "k_step.cu"}
+
+
+def kernel_source_hash(kernel=None):
+    """Hash of what one kernel is compiled from: its .cu file, the library's headers and the
+    build script (flags); kernel=None covers every source file of the library (launch lists).
+    A recorded ncu figure is used only while this hash is unchanged."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2406_09654_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        h.update(open(os.path.join(d, f), "rb").read())
+    units = [KERNEL_UNITS[kernel]] if kernel else [f for f in sorted(os.listdir(d)) if f.endswith(".cu")]
+    files = [os.path.join(d, u) for u in units]
+    files += [os.path.join(d, f) for f in sorted(os.listdir(d)) if f.endswith((".cuh", ".h"))]
+    files += [os.path.join(ROOT, "include", f) for f in sorted(os.listdir(os.path.join(ROOT, "include")))]
+    files.append(os.path.join(ROOT, "paper_2406_09654_gb300", "build.py"))
+    for f in files:
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel, workload):
-    """DRAM bytes per launch from a committed ncu summary, if the kernel sources are unchanged."""
+    """DRAM bytes per launch from a committed ncu summary, if the kernel's sources are unchanged."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p))
     e = d.get(f"{kernel}@{workload}")
-    if not e or e.get("source_hash") != kernel_source_hash():
+    if not e or e.get("source_hash") != kernel_source_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 

@@ -444,19 +444,34 @@ __global__ void __launch_bounds__(128) k_rad_assign(RadiationArgs r) {
 // ---------------------------------------------------------------------------------------
 constexpr int kSortThreads = 256;
 constexpr int kSortTile = 4096;
+constexpr int kSortItems = kSortTile / kSortThreads;    // keys per thread
+static_assert(kSortThreads == 256, "one thread per digit value in the scatter's offsets");
+// Element layout of a block's tile in the histogram, scatter and run kernels: warp w owns the
+// contiguous range [w * 512, w * 512 + 512) of the tile; in item c, lane l holds element
+// w * 512 + 32 c + l. Every thread loads its 16 keys before it uses any of them, so a warp
+// has 16 coalesced 128-byte loads in flight instead of one.
+__device__ __forceinline__ long long sort_elem0(int lane, int w) {
+  return (long long)blockIdx.x * kSortTile + w * (kSortItems * 32) + lane;
+}
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const int32_t* keys, long long N, int shift,
-                                                          int32_t* hist, int nblk) {
+__global__ void __launch_bounds__(kSortThreads) k_sort_hist(const int32_t* __restrict__ keys, long long N,
+                                                          int shift, int32_t* hist, int nblk) {
   __shared__ int h[256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long e0 = sort_elem0(lane, w);
+  int d[kSortItems];
+#pragma unroll
+  for (int c = 0; c < kSortItems; ++c) {
+    const long long j = e0 + 32 * c;
+    d[c] = j < N ? (__ldg(keys + j) >> shift) & 255 : 256;
+  }
   h[threadIdx.x] = 0;
   __syncthreads();
-  const long long base = (long long)blockIdx.x * kSortTile;
-  for (int i = threadIdx.x; i < kSortTile; i += kSortThreads) {
-    const long long j = base + i;
-    const int d = j < N ? (keys[j] >> shift) & 255 : 256;
+#pragma unroll
+  for (int c = 0; c < kSortItems; ++c) {
     // one shared-memory add per distinct digit of the warp (genomes come in runs)
-    const unsigned m = __match_any_sync(0xffffffffu, d);
-    if (d < 256 && (threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(&h[d], __popc(m));
+    const unsigned m = __match_any_sync(0xffffffffu, d[c]);
+    if (d[c] < 256 && lane == __ffs(m) - 1) atomicAdd(&h[d[c]], __popc(m));
   }
   __syncthreads();
   hist[(long long)threadIdx.x * nblk + blockIdx.x] = h[threadIdx.x];
@@ -479,22 +494,29 @@ __global__ void __launch_bounds__(256) k_digit_totals(const int32_t* hist, int n
 }
 
 // Exclusive scan of the histograms in digit-major order, one block per digit value: row d
-// starts at the keys of smaller digits and runs over the blocks in order (in place).
+// starts at the keys of smaller digits and runs over the blocks in order (in place). Each
+// thread takes 4 consecutive entries, so a row of up to 4096 blocks is one pass.
 __global__ void __launch_bounds__(1024) k_digit_scan(int32_t* hist, int nblk, const int32_t* totals) {
   __shared__ int wsum[32];
-  __shared__ int carry;
+  __shared__ int base_s;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) {
-    int base = 0;
-    for (int d = 0; d < (int)blockIdx.x; ++d) base += totals[d];
-    carry = base;
+  if (w == 0) {
+    int v = 0;
+    for (int d = lane; d < (int)blockIdx.x; d += 32) v += totals[d];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) base_s = v;
   }
   __syncthreads();
+  int carry = base_s;
   int32_t* row = hist + (long long)blockIdx.x * nblk;
-  for (int c0 = 0; c0 < nblk; c0 += 1024) {
-    const int b = c0 + threadIdx.x;
-    const int v = b < nblk ? row[b] : 0;
-    int inc = v;
+  for (int c0 = 0; c0 < nblk; c0 += 4 * 1024) {
+    const int b0 = c0 + 4 * threadIdx.x;
+    int v[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = b0 + i < nblk ? row[b0 + i] : 0;
+    const int sum = v[0] + v[1] + v[2] + v[3];
+    int inc = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int t = __shfl_up_sync(0xffffffffu, inc, o);
@@ -504,66 +526,103 @@ __global__ void __launch_bounds__(1024) k_digit_scan(int32_t* hist, int nblk, co
     __syncthreads();
     int before = carry, tot = 0;
     for (int i = 0; i < 32; ++i) {
-      if (i < w) before += wsum[i];
-      tot += wsum[i];
+      const int s = wsum[i];
+      if (i < w) before += s;
+      tot += s;
     }
-    if (b < nblk) row[b] = before + inc - v;
-    __syncthreads();
-    if (threadIdx.x == 0) carry += tot;
-    __syncthreads();
+    int run = before + inc - sum;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if (b0 + i < nblk) row[b0 + i] = run;
+      run += v[i];
+    }
+    carry += tot;
+    __syncthreads();                                  // wsum is rewritten by the next chunk
   }
 }
 
 // Keys per slot from the sorted keys: each block takes a contiguous chunk; a run of equal keys
 // inside it adds (last - c0 + 1) at its last element and -(first - c0) at its first, so each
 // slot receives the total length of its runs with two atomics per run and chunk.
-__global__ void __launch_bounds__(kSortThreads) k_count_runs(const int32_t* sk, long long N, int cap,
+__global__ void __launch_bounds__(kSortThreads) k_count_runs(const int32_t* __restrict__ sk, long long N, int cap,
                                                            int32_t* count) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long c0 = (long long)blockIdx.x * kSortTile;
   const long long c1 = c0 + kSortTile < N ? c0 + kSortTile : N;
-  for (long long i = c0 + threadIdx.x; i < c1; i += kSortThreads) {
-    const int k = sk[i];
-    if (k < 0 || k >= cap) continue;
-    if (i == c0 || sk[i - 1] != k) atomicAdd(&count[k], -(int)(i - c0));
-    if (i == c1 - 1 || sk[i + 1] != k) atomicAdd(&count[k], (int)(i - c0 + 1));
+  const long long e0 = sort_elem0(lane, w);
+  int k[kSortItems];
+#pragma unroll
+  for (int c = 0; c < kSortItems; ++c) {
+    const long long j = e0 + 32 * c;
+    k[c] = j < c1 ? __ldg(sk + j) : -1;
+  }
+#pragma unroll
+  for (int c = 0; c < kSortItems; ++c) {
+    const long long j = e0 + 32 * c;
+    // neighbours in the sorted order: the adjacent lanes, or memory at the warp's edges
+    int prev = __shfl_up_sync(0xffffffffu, k[c], 1);
+    int next = __shfl_down_sync(0xffffffffu, k[c], 1);
+    if (lane == 0 && j > c0 && j < c1) prev = __ldg(sk + j - 1);
+    if (lane == 31 && j + 1 < c1) next = __ldg(sk + j + 1);
+    const int key = k[c];
+    if (j >= c1 || key < 0 || key >= cap) continue;
+    const bool head = j == c0 || prev != key;
+    const bool tail = j == c1 - 1 || next != key;
+    if (head && tail) atomicAdd(&count[key], 1);
+    else if (head) atomicAdd(&count[key], -(int)(j - c0));
+    else if (tail) atomicAdd(&count[key], (int)(j - c0 + 1));
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const int32_t* kin, const int32_t* vin,
-                                                             int32_t* kout, int32_t* vout, long long N,
-                                                             int shift, const int32_t* off, int nblk) {
-  __shared__ int wcnt[kSortThreads / 32][257];
-  __shared__ int run[256];
+// One stable 256-bucket pass. Each warp ranks its own contiguous 512 keys (a running count
+// per digit value in its row of shared memory), then thread t turns digit t's per-warp counts
+// into start positions after the block's offset for that digit: two CTA barriers per block.
+__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const int32_t* __restrict__ kin,
+                                                             const int32_t* __restrict__ vin, int32_t* kout,
+                                                             int32_t* vout, long long N, int shift,
+                                                             const int32_t* off, int nblk) {
+  __shared__ int wc[kSortThreads / 32][256];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  run[threadIdx.x] = off[(long long)threadIdx.x * nblk + blockIdx.x];
-  for (int i = 0; i < kSortThreads / 32; ++i) wcnt[i][threadIdx.x] = 0;
-  __syncthreads();
-  const long long base = (long long)blockIdx.x * kSortTile;
-  for (int c0 = 0; c0 < kSortTile; c0 += kSortThreads) {
-    const long long j = base + c0 + threadIdx.x;
+  const long long e0 = sort_elem0(lane, w);
+  int key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+  for (int c = 0; c < kSortItems; ++c) {
+    const long long j = e0 + 32 * c;
     const bool ok = j < N;
-    const int key = ok ? kin[j] : 0;
-    const int val = ok ? (vin ? vin[j] : (int)j) : 0;
-    const int d = ok ? (key >> shift) & 255 : 256;
+    key[c] = ok ? __ldg(kin + j) : 0;
+    val[c] = ok ? (vin ? __ldg(vin + j) : (int)j) : 0;
+  }
+  for (int i = lane; i < 256; i += 32) wc[w][i] = 0;
+  __syncwarp();
+  const unsigned lower = (1u << lane) - 1u;
+#pragma unroll
+  for (int c = 0; c < kSortItems; ++c) {
+    const int d = e0 + 32 * c < N ? (key[c] >> shift) & 255 : 256;
     const unsigned m = __match_any_sync(0xffffffffu, d);
-    const int rank = __popc(m & ((1u << lane) - 1));
-    if (lane == __ffs(m) - 1) wcnt[w][d] = __popc(m);
-    __syncthreads();
-    if (ok) {
-      int pre = 0;
-      for (int i = 0; i < w; ++i) pre += wcnt[i][d];
-      const int pos = run[d] + pre + rank;
-      kout[pos] = key;
-      vout[pos] = val;
-    }
-    __syncthreads();
-    int add = 0;
+    const int before = d < 256 ? wc[w][d] : 0;
+    rank[c] = before + __popc(m & lower);
+    __syncwarp();
+    if (d < 256 && lane == __ffs(m) - 1) wc[w][d] = before + __popc(m);
+    __syncwarp();
+  }
+  __syncthreads();
+  {
+    int acc = off[(long long)threadIdx.x * nblk + blockIdx.x];
+#pragma unroll
     for (int i = 0; i < kSortThreads / 32; ++i) {
-      add += wcnt[i][threadIdx.x];
-      wcnt[i][threadIdx.x] = 0;
+      const int t = wc[i][threadIdx.x];
+      wc[i][threadIdx.x] = acc;
+      acc += t;
     }
-    run[threadIdx.x] += add;
-    __syncthreads();
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < kSortItems; ++c) {
+    if (e0 + 32 * c < N) {
+      const int pos = wc[w][(key[c] >> shift) & 255] + rank[c];
+      kout[pos] = key[c];
+      vout[pos] = val[c];
+    }
   }
 }
 

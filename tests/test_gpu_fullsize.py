@@ -79,3 +79,20 @@ def test_fullsize_radiation_event_bit_exact(cfg3):
             assert np.allclose(genes[k], gen2.genes[k], rtol=0, atol=2e-6)
     finally:
         w.physics = dict(w.physics, k_exp=0.5, radiation_every=20)
+
+
+def test_fullsize_bucketing_sort(cfg3):
+    """The bucketing sort of the full-size world's GenomeIndex (the sort bench.py times). A
+    permutation whose keys are non-decreasing and whose cell ids increase within each key is
+    the stable sort, so these properties check every output; counts against a plain bincount."""
+    G = cfg3.G.ravel().astype(np.int64)
+    with coral.Substrate(coral.params_from_world(cfg3), cfg3.width, cfg3.height, cfg3.capacity) as sub:
+        sub.load_state(cfg3.E, cfg3.I, cfg3.C, cfg3.G, cfg3.R)
+        counts, perm = sub.read_perm()
+    n = G.size
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    k = G[perm]
+    assert np.all(np.diff(k) >= 0)
+    same = k[1:] == k[:-1]
+    assert np.all(np.diff(perm.astype(np.int64))[same] > 0)
+    assert np.array_equal(counts, np.bincount(G, minlength=cfg3.capacity))

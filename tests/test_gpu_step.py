@@ -179,7 +179,9 @@ def test_dense_nets_round_trip():
 
 
 @pytest.mark.parametrize("W,H,cap,layout", [(50, 40, 300, "random"), (64, 64, 8, "voronoi"),
-                                            (33, 31, 70000, "random"), (3, 3, 1, "voronoi")])
+                                            (33, 31, 70000, "random"), (3, 3, 1, "voronoi"),
+                                            (300, 250, 300, "random"), (300, 250, 70000, "random"),
+                                            (257, 255, 4000, "voronoi")])
 def test_bucket_counting_sort_bit_exact(W, H, cap, layout):
     n = min(cap, 200)
     w = worlds.make_world(width=W, height=H, n_genomes=max(1, min(n, W * H)), layout=layout, seed=W, capacity=cap)
