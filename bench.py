@@ -387,12 +387,18 @@ def run_coral(a, rank, world_size, local):
         out = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
         sub.step_jobs([host], [out], 1, t)                      # staging buffers, first use
         torch.cuda.synchronize()
-        barrier(world_size)
-        t0 = time.perf_counter()
-        sub.step_jobs([host] * a.e2e_steps, [out] * a.e2e_steps, 1, t)
-        el = max_over_ranks(time.perf_counter() - t0, world_size)
-        e2e = {"value": N * a.e2e_steps * world_size / el, "unit": "cell-updates/s",
-               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+        # three windows of e2e_steps jobs each, the median reported: single windows of the same
+        # build have differed by a quarter from one run to the next
+        rates = []
+        for _ in range(3):
+            barrier(world_size)
+            t0 = time.perf_counter()
+            sub.step_jobs([host] * a.e2e_steps, [out] * a.e2e_steps, 1, t)
+            el = max_over_ranks(time.perf_counter() - t0, world_size)
+            rates.append(N * a.e2e_steps * world_size / el)
+        e2e = {"value": float(np.median(rates)), "unit": "cell-updates/s",
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+               "windows": [float(r) for r in rates]}
     # bucketing (stable counting sort of the cells by GenomeIndex) of the final state, device
     # time of the sort kernels on the substrate's stream (the call then synchronises)
     bucket = None

@@ -41,6 +41,7 @@ struct coral_substrate {
   bool genomes_loaded = false;
   bool has_cppn = false;
   Partial* part1 = nullptr;
+  int* sched = nullptr;         // pass 1's tile pool counters
   Partial* part2 = nullptr;
   coral_stats* ring = nullptr;
   int* status = nullptr;
@@ -129,6 +130,7 @@ StepArgs step_args(const coral_substrate* s) {
   a.day_period = s->p.day_period;
   a.capacity = s->cap;
   a.step_dev = nullptr;
+  a.sched = s->sched;
   return a;
 }
 
@@ -234,7 +236,8 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
          dalloc(s, &s->g.nets32, (size_t)genome_capacity * s->g.net_stride) == cudaSuccess &&
          dalloc(s, &s->g.nets16, (size_t)genome_capacity * s->g.blob_bytes) == cudaSuccess;
     ok = ok && dalloc(s, &s->part1, kMaxPartials) == cudaSuccess && dalloc(s, &s->part2, kMaxPartials) == cudaSuccess &&
-         dalloc(s, &s->ring, kRing) == cudaSuccess && dalloc(s, &s->status, 4) == cudaSuccess;
+         dalloc(s, &s->ring, kRing) == cudaSuccess && dalloc(s, &s->status, 4) == cudaSuccess &&
+         dalloc(s, &s->sched, 2) == cudaSuccess;
     const int nblk = radiation_blocks(N);
     // per-block counts of the hit passes (cells) and of the free-slot passes (slots)
     const int nbc = std::max(nblk, (genome_capacity + 1023) / 1024);
@@ -250,6 +253,7 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
       break;
     }
     if ((e = cudaMemset(s->status, 0, 4 * sizeof(int))) != cudaSuccess ||
+        (e = cudaMemset(s->sched, 0, 2 * sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(s->ring, 0, kRing * sizeof(coral_stats))) != cudaSuccess ||
         (e = cudaMemset(s->g.parent, 0xFF, sizeof(int32_t) * genome_capacity)) != cudaSuccess ||
         (e = cudaMemset(s->g.genes, 0, sizeof(float) * kGenes * genome_capacity)) != cudaSuccess ||

@@ -105,6 +105,8 @@ struct __align__(8) StepArgs {
   int capacity;     // genome slots: a GenomeIndex outside [0, capacity) acts as "no genome"
   const long long* step_dev;   // batched stepping: this world's step index on the device (day/night
                                // is taken from it); NULL: use is_day
+  int* sched;                  // BF16 pass 1's tile pool: [0] next chunk, [1] CTAs done (both 0
+                               // between launches: the last CTA of a launch resets them)
 };
 
 // Batched stepping of many worlds (same hidden size, BF16 path): the CTAs of each launch are

@@ -30,6 +30,16 @@ constexpr int kHaloW = kTileW + 2, kHaloH = kTileH + 2;
 constexpr int kHaloCells = kHaloW * kHaloH;
 constexpr uint32_t kTmemCols = 64;                        // layer 1, then layer 2 in cols 0..15
 constexpr long long kWaitCycles = 4000000000LL;           // about 2 s of SM clock
+// Work split: each CTA first takes a contiguous run of about 3/4 of its share of the tiles
+// (neighbouring tiles share halo rows in L2 and usually a genome); the remaining tiles form a
+// pool of kChunk-tile chunks that CTAs claim with one atomic each as they finish, so CTAs
+// whose tiles hold more genomes (more rounds) no longer set the kernel's end.
+constexpr int kStaticNum = 3, kStaticDen = 4;
+constexpr int kChunk = 4;
+// C' sums in fixed point: every float in [2^-3, 1) is a multiple of 2^-26 and C' lies in
+// (0.26, 0.74), so C' * 2^26 is an exact integer and the sums are exact, independent of which
+// CTA took which tile (and so of the order in which the pool was claimed).
+constexpr float kCFix = 67108864.0f;                      // 2^26
 
 // shared memory layout, offsets from a 1024-byte aligned base
 constexpr int kOffA = 0;                                  // 128 x 128 B: input tile, then hidden tile
@@ -109,7 +119,8 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   unsigned* ballots = reinterpret_cast<unsigned*>(base + kOffMisc + 16);      // [2][4] pending rows
   uint64_t* halo_bar = reinterpret_cast<uint64_t*>(base + kOffMisc + 48);     // the stage's TMA barrier
   unsigned* match = reinterpret_cast<unsigned*>(base + kOffMisc + 64);        // [4] rows of the staged genome
-  __shared__ double red_s[4][4];
+  int* claim_s = reinterpret_cast<int*>(base + kOffMisc + 80);                // [2] pool chunks claimed by thread 0
+  __shared__ long long red_s[4][4];
   __shared__ long long red_c[4];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -139,9 +150,9 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   const uint32_t idesc2 = tc::idesc_bf16_f32(128, 16);
   uint32_t phase = 0;
 
-  if (lane == 0) {                                    // this warp's FP64 sums of C'
+  if (lane == 0) {                                    // this warp's fixed-point sums of C'
 #pragma unroll
-    for (int k = 0; k < 4; ++k) red_s[warp][k] = 0.0;
+    for (int k = 0; k < 4; ++k) red_s[warp][k] = 0;
   }
   int accX = 0;
   bool timed_out = false;                             // the CTA agreed to stop (a wait ran out)
@@ -150,10 +161,19 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   int rb = 0;                                         // ballot buffer the next round reads
   const int tiles_x = (W + kTileW - 1) / kTileW, tiles_y = (Hh + kTileH - 1) / kTileH;
   const int n_tiles = tiles_x * tiles_y;
-  // a contiguous run of tiles per CTA: neighbouring tiles share halo rows (L2) and genomes
-  const int per = (n_tiles + ncta - 1) / ncta;
-  const int t_begin = cta * per;
-  const int t_end = t_begin + per < n_tiles ? t_begin + per : n_tiles;
+  // this CTA's contiguous run, then chunks of the pool [pool0, n_tiles)
+  const int per = (int)((long long)n_tiles * kStaticNum / kStaticDen / ncta);
+  const int pool0 = per * ncta;
+  // the pool chunk claimed as number q: its first tile, or -1 when the pool is used up
+  auto chunk_first = [&](int q) { return q < (n_tiles - pool0 + kChunk - 1) / kChunk ? pool0 + q * kChunk : -1; };
+  int cur = cta * per, run_end = cur + per;
+  if (per == 0) {                                     // small world: the pool only
+    if (tid == 0) claim_s[0] = atomicAdd(a.sched, 1);
+    __syncthreads();
+    cur = chunk_first(claim_s[0]);
+    run_end = cur < 0 ? -1 : min(cur + kChunk, n_tiles);
+    __syncthreads();                                  // claim_s[0] is written again below
+  }
   int g_next = -1, r_next = 0;
   uint32_t halo_phase = 0;                            // parity of halo_bar
   bool tma_pending = false;                           // a TMA copy into the stage is in flight
@@ -184,27 +204,37 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       r_next = a.rotation ? (int)__ldg(a.cur.R + jn) : 0;
     }
   };
-  int tx = t_begin % tiles_x, ty = t_begin / tiles_x;   // running tile coordinates
-  if (t_begin < t_end) prefetch(tx * kTileW, ty * kTileH);
-  float cacc[4] = {0, 0, 0, 0};           // FP32 partials of up to 16 tiles, then into red_s
-  // adds the partials of this warp's 32 threads in FP64 (fixed tree) to its row of red_s
+  int ty = cur < 0 ? 0 : cur / tiles_x, tx = cur < 0 ? 0 : cur - ty * tiles_x;   // running tile coordinates
+  if (cur >= 0) prefetch(tx * kTileW, ty * kTileH);
+  int cacc[4] = {0, 0, 0, 0};             // fixed-point partials of up to 16 tiles (< 2^31), then into red_s
+  // adds the partials of this warp's 32 threads (64-bit integers) to its row of red_s
   auto flush = [&]() {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      double v = (double)cacc[k];
+      long long v = cacc[k];
 #pragma unroll
       for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
       if (lane == 0) red_s[warp][k] += v;
-      cacc[k] = 0.0f;
+      cacc[k] = 0;
     }
   };
   int ntile = 0;
+  int it = 0;                                         // tile count: parity selects claim_s
+  int reserved = -2;                                  // thread 0: pool chunk claimed ahead (-2: none)
 
-  for (int tile = t_begin; tile < t_end; ++tile) {
+  while (cur >= 0) {
     const int x0 = tx * kTileW, y0 = ty * kTileH;
-    if (++tx == tiles_x) {
-      tx = 0;
-      ++ty;
+    // the next tile: the next one of this run, or the first of a newly claimed pool chunk
+    // (claimed now, read after the records barrier; two slots, so that a slow thread still
+    // reading the last claim never sees it overwritten)
+    const bool claim = cur + 1 >= run_end;
+    if (tid == 0) {
+      // the atomic is issued one tile ahead of the claim, so its latency is not waited for
+      if (reserved == -2 && cur + 2 >= run_end) reserved = atomicAdd(a.sched, 1);
+      if (claim) {
+        claim_s[it & 1] = reserved;
+        reserved = -2;
+      }
     }
     const int gx = x0 + lx, gy = y0 + ly;
     const bool valid = gx < W && gy < Hh;
@@ -255,7 +285,21 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       timed_out = true;
       break;
     }
-    if (tile + 1 < t_end) prefetch(tx * kTileW, ty * kTileH);
+    int nxt = cur + 1, nxt_end = run_end;
+    if (claim) {
+      nxt = chunk_first(claim_s[it & 1]);
+      nxt_end = nxt < 0 ? -1 : min(nxt + kChunk, n_tiles);
+    }
+    if (nxt >= 0) {
+      if (claim) {
+        ty = nxt / tiles_x;
+        tx = nxt - ty * tiles_x;
+      } else if (++tx == tiles_x) {
+        tx = 0;
+        ++ty;
+      }
+      prefetch(tx * kTileW, ty * kTileH);
+    }
     const int hc = (ly + 1) * kHaloW + (lx + 1);
     const uint32_t row_s = a_s + tid * 128;
     // actuator epilogue and pass-1 stores of this thread's cell, in the round that finishes it
@@ -264,7 +308,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       actuator_epilogue<true>(a, act, zo, Ec, Ic, Sf, r, o);
       store_pass1(a, j, o);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) cacc[k] += o.C[k];
+      for (int k = 0; k < 4; ++k) cacc[k] += __float2int_rn(o.C[k] * kCFix);
       accX += o.xdir != kNoExplore ? 1 : 0;
     };
     if (valid && g < 0) {                             // empty cell: all actuators at zero
@@ -418,6 +462,9 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       ntile = 0;
       flush();
     }
+    cur = nxt;
+    run_end = nxt_end;
+    ++it;
   }
   tc::cp_async_wait_all();                            // no copy may land after the CTA exits
   if (tid == 0 && tma_pending) tc::mbar_wait(halo_bar, halo_phase, kWaitCycles);
@@ -431,11 +478,22 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   if (__syncthreads_or(bad || timed_out) && tid == 0) atomicCAS(a.status, 0, (int)CORAL_E_TIMEOUT);
   if (tid == 0) {
     Partial p = {};
+    long long cs[4] = {0, 0, 0, 0};
     for (int w = 0; w < 4; ++w) {
-      for (int k = 0; k < 4; ++k) p.s[2 + k] += red_s[w][k];
+      for (int k = 0; k < 4; ++k) cs[k] += red_s[w][k];
       p.c[0] += red_c[w];
     }
+    // exact in FP64 (integers below 2^53 times a power of two), and so are the FP64 sums of
+    // these partials: the totals do not depend on the order of the partials
+    for (int k = 0; k < 4; ++k) p.s[2 + k] = (double)cs[k] / (double)kCFix;
     a.part1[cta] = p;
+    // the pool is free again for the next launch: the last CTA to finish resets its counters
+    __threadfence();
+    if (atomicAdd(a.sched + 1, 1) == ncta - 1) {
+      a.sched[0] = 0;
+      a.sched[1] = 0;
+      __threadfence();
+    }
   }
   if (warp == 0) {
     tc::tc_fence_after();

@@ -48,6 +48,8 @@ def test_batched_equals_alone_bit_exact():
             bs = s.read_stats(4, 1)[0]
             assert bs["step"] == 4 and bs["n_explore"] == st["n_explore"]
             assert bs["sum_E"] == pytest.approx(st["sum_E"], rel=1e-12)
+            # the C' totals are exact sums, whatever the split of tiles among CTAs
+            assert bs["sum_C"] == st["sum_C"]
             assert s.get_step() == 5
     finally:
         for s in subs:
