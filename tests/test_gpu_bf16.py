@@ -59,7 +59,11 @@ def forced(world, steps, tol, tau, t0=0, net_precision="fp64", max_band_frac=Non
 
 @pytest.mark.parametrize("W,H,n,hidden,layout", [(64, 64, 8, 0, "voronoi"), (96, 40, 6, 32, "voronoi"),
                                                  (37, 29, 5, 64, "voronoi"), (33, 7, 3, 16, "voronoi"),
-                                                 (64, 64, 9, 48, "voronoi"), (40, 24, 50, 64, "random")])
+                                                 (64, 64, 9, 48, "voronoi"), (40, 24, 50, 64, "random"),
+                                                 # rows not a multiple of 16 bytes: the halo of interior
+                                                 # tiles comes by bulk row copies with per-row shifts
+                                                 (130, 70, 10, 64, "voronoi"), (141, 43, 8, 32, "random"),
+                                                 (103, 37, 6, 16, "voronoi")])
 def test_bf16_matches_bf16_operand_oracle(W, H, n, hidden, layout):
     w = worlds.make_world(width=W, height=H, n_genomes=n, hidden=hidden, layout=layout,
                           net="cppn" if hidden else "direct", seed=W + H + hidden, random_rotation=True)
