@@ -17,6 +17,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import statistics
 import subprocess
@@ -170,10 +171,22 @@ def measured_peaks():
 KERNEL_UNITS = {"pass1_bf16": "k_bf16.cu", "pass1_fp32": "k_step.cu", "pass2": "k_step.cu"}
 
 
+def _code_only(path):
+    """A source file's bytes with its comments and blank lines removed (C/C++ files), so that a
+    comment edit does not count as a change of the compiled kernel."""
+    data = open(path, "rb").read()
+    if not path.endswith((".cu", ".cuh", ".h")):
+        return data
+    text = data.decode()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(l.rstrip() for l in text.splitlines() if l.strip()).encode()
+
+
 def kernel_source_hash(kernel=None):
     """Hash of what one kernel is compiled from: its .cu file, the library's headers and the
-    build script (flags); kernel=None covers every source file of the library (launch lists).
-    A recorded ncu figure is used only while this hash is unchanged."""
+    build script (flags), comments left out; kernel=None covers every source file of the
+    library (launch lists). A recorded ncu figure is used only while this hash is unchanged."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2406_09654_gb300", "csrc")
     units = [KERNEL_UNITS[kernel]] if kernel else [f for f in sorted(os.listdir(d)) if f.endswith(".cu")]
@@ -183,7 +196,7 @@ def kernel_source_hash(kernel=None):
     files.append(os.path.join(ROOT, "paper_2406_09654_gb300", "build.py"))
     for f in files:
         h.update(os.path.basename(f).encode())
-        h.update(open(f, "rb").read())
+        h.update(_code_only(f))
     return h.hexdigest()[:16]
 
 

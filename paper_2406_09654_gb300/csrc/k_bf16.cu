@@ -1,5 +1,5 @@
 // BF16 tensor-core network (pass 1) on tcgen05: each CTA takes a contiguous run of 32x4-cell
-// tiles of the torus. A tile's one-cell halo of the six sensor channels comes into shared memory
+// tiles of the torus, then chunks of tiles from a shared pool. A tile's one-cell halo of the six sensor channels comes into shared memory
 // by one TMA box copy (cp.async where the halo wraps around the torus); the CTA turns it into
 // BF16 cell records and takes each cell's own E, I and flow denominator from it, after which the
 // buffer is free and the next tile's copy overlaps this tile's network. From the records it
@@ -104,8 +104,8 @@ __device__ __forceinline__ void issue_halo(const StepArgs& a, int x0, int y0, ui
   tc::cp_async_commit();
 }
 
-// One CTA's share of pass 1 for one world: CTA `cta` of `ncta` takes a contiguous run of tiles;
-// its partial sums go to a.part1[cta]. tmap: TMA descriptor (use_tma != 0) or unused.
+// One CTA's share of pass 1 for one world: CTA `cta` of `ncta` takes a contiguous run of tiles,
+// then pool chunks (see kStaticNum); its partial sums go to a.part1[cta]. tmap: TMA descriptor (use_tma != 0) or unused.
 // kH: the hidden size (0 = one layer), a compile-time constant so that the per-chunk loops and
 // the layer-2 branch are resolved by the compiler; one instantiation per supported size.
 template <int kH>
