@@ -577,20 +577,24 @@ __global__ void __launch_bounds__(kSortThreads) k_count_runs(const int32_t* __re
 // One stable 256-bucket pass. Each warp ranks its own contiguous 512 keys (a running count
 // per digit value in its row of shared memory), then thread t turns digit t's per-warp counts
 // into start positions after the block's offset for that digit: two CTA barriers per block.
-__global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const int32_t* __restrict__ kin,
-                                                             const int32_t* __restrict__ vin, int32_t* kout,
-                                                             int32_t* vout, long long N, int shift,
-                                                             const int32_t* off, int nblk) {
+// kVal: values come from vin (later passes); else the value is the key's index (first pass).
+// Three blocks per SM (80 registers: ranks packed two per register).
+template <bool kVal>
+__global__ void __launch_bounds__(kSortThreads, 3) k_sort_scatter(const int32_t* __restrict__ kin,
+                                                                const int32_t* __restrict__ vin, int32_t* kout,
+                                                                int32_t* vout, long long N, int shift,
+                                                                const int32_t* off, int nblk) {
   __shared__ int wc[kSortThreads / 32][256];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long e0 = sort_elem0(lane, w);
-  int key[kSortItems], val[kSortItems], rank[kSortItems];
+  int key[kSortItems], val[kSortItems];
+  uint32_t rank[kSortItems / 2];                      // ranks (< 512) of items 2i, 2i+1 in 16-bit halves
 #pragma unroll
   for (int c = 0; c < kSortItems; ++c) {
     const long long j = e0 + 32 * c;
     const bool ok = j < N;
     key[c] = ok ? __ldg(kin + j) : 0;
-    val[c] = ok ? (vin ? __ldg(vin + j) : (int)j) : 0;
+    if (kVal) val[c] = ok ? __ldg(vin + j) : 0;
   }
   for (int i = lane; i < 256; i += 32) wc[w][i] = 0;
   __syncwarp();
@@ -600,7 +604,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const int32_t* __
     const int d = e0 + 32 * c < N ? (key[c] >> shift) & 255 : 256;
     const unsigned m = __match_any_sync(0xffffffffu, d);
     const int before = d < 256 ? wc[w][d] : 0;
-    rank[c] = before + __popc(m & lower);
+    const uint32_t rk = (uint32_t)(before + __popc(m & lower));
+    if (c & 1) rank[c >> 1] |= rk << 16;
+    else rank[c >> 1] = rk;
     __syncwarp();
     if (d < 256 && lane == __ffs(m) - 1) wc[w][d] = before + __popc(m);
     __syncwarp();
@@ -619,9 +625,9 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_scatter(const int32_t* __
 #pragma unroll
   for (int c = 0; c < kSortItems; ++c) {
     if (e0 + 32 * c < N) {
-      const int pos = wc[w][(key[c] >> shift) & 255] + rank[c];
+      const int pos = wc[w][(key[c] >> shift) & 255] + (int)((rank[c >> 1] >> (16 * (c & 1))) & 0xFFFFu);
       kout[pos] = key[c];
-      vout[pos] = val[c];
+      vout[pos] = kVal ? val[c] : (int)(e0 + 32 * c);
     }
   }
 }
@@ -720,7 +726,10 @@ cudaError_t launch_bucket(const SortArgs& a, cudaStream_t st) {
     k_sort_hist<<<nblk, kSortThreads, 0, st>>>(kin, a.N, 8 * p, a.hist, nblk);
     k_digit_totals<<<256, 256, 0, st>>>(a.hist, nblk, a.totals);
     k_digit_scan<<<256, 1024, 0, st>>>(a.hist, nblk, a.totals);
-    k_sort_scatter<<<nblk, kSortThreads, 0, st>>>(kin, vin, kout, vout, a.N, 8 * p, a.hist, nblk);
+    if (vin)
+      k_sort_scatter<true><<<nblk, kSortThreads, 0, st>>>(kin, vin, kout, vout, a.N, 8 * p, a.hist, nblk);
+    else
+      k_sort_scatter<false><<<nblk, kSortThreads, 0, st>>>(kin, vin, kout, vout, a.N, 8 * p, a.hist, nblk);
     kin = kout;
     vin = vout;
   }
