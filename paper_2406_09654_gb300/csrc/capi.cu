@@ -271,6 +271,11 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
       rc = fail(s, CORAL_E_CUDA, "the BF16 tensor-core kernel cannot be launched on this device");
       break;
     }
+    // small worlds: no more CTAs than units of work (pass-1 tiles; pass-2 chunks of 4 cells,
+    // 256 per CTA), so that CTAs without work do not pay for their setup every step
+    if (p->path == CORAL_NET_BF16_GROUPED)
+      s->grid1 = (int)std::min<long long>(s->grid1, pass1_bf16_tiles(width, height));
+    s->grid2 = (int)std::min<long long>(s->grid2, (N + 1023) / 1024);
   } while (0);
   if (rc != CORAL_OK) {
     free_all(s);
