@@ -713,6 +713,8 @@ struct coral_batch {
   int* d_part = nullptr;         // cta_world1 | first1 | ctas1 | cta_world2 | first2 | ctas2
   coral_stats** d_rings = nullptr;
   long long* d_steps = nullptr;
+  CUtensorMap* d_tmaps = nullptr;  // [2][n]
+  int* d_tma_ok = nullptr;         // [n]
   int cps1 = 5, cps2 = 3;        // CTAs per SM of pass 1 / pass 2
   int grid1 = 0, grid2 = 0;
   int max_grid = 0;
@@ -786,6 +788,8 @@ BatchTable table_of(const coral_batch* b) {
   t.world_ctas2 = b->d_part + 2 * g + 3 * b->n;
   t.rings = b->d_rings;
   t.steps = b->d_steps;
+  t.tmaps = b->d_tmaps;
+  t.tma_ok = b->d_tma_ok;
   return t;
 }
 
@@ -861,9 +865,12 @@ int batch_leave(coral_batch* b, int n_steps) {
   return CORAL_OK;
 }
 
-// The worlds' step arguments for both parities relative to their current buffers.
+// The worlds' step arguments and TMA descriptors for both parities relative to their current
+// buffers.
 int batch_upload_args(coral_batch* b) {
   std::vector<StepArgs> args(2 * (size_t)b->n);
+  std::vector<CUtensorMap> maps(2 * (size_t)b->n);
+  std::vector<int> ok(b->n, 0);
   for (int p = 0; p < 2; ++p)
     for (int i = 0; i < b->n; ++i) {
       coral_substrate* s = b->worlds[i];
@@ -873,8 +880,13 @@ int batch_upload_args(coral_batch* b) {
       s->cur = save;
       a.step_dev = b->d_steps + i;
       args[(size_t)p * b->n + i] = a;
+      if (s->tmap_ok) maps[(size_t)p * b->n + i] = s->tmap[save ^ p];
+      else memset(&maps[(size_t)p * b->n + i], 0, sizeof(CUtensorMap));
+      ok[i] = s->tmap_ok ? 1 : 0;
     }
   BCK(b, cudaMemcpyAsync(b->d_args, args.data(), sizeof(StepArgs) * args.size(), cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaMemcpyAsync(b->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(), cudaMemcpyHostToDevice, b->stream));
+  BCK(b, cudaMemcpyAsync(b->d_tma_ok, ok.data(), sizeof(int) * ok.size(), cudaMemcpyHostToDevice, b->stream));
   BCK(b, cudaStreamSynchronize(b->stream));
   return CORAL_OK;
 }
@@ -911,7 +923,8 @@ extern "C" int coral_batch_create(coral_substrate* const* worlds, int32_t n, cor
     cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
     const size_t bytes = sizeof(StepArgs) * 2 * (size_t)n + 256 + sizeof(int) * (4 * (size_t)b->max_grid + 6 * (size_t)n) +
-                         256 + sizeof(coral_stats*) * (size_t)n + 256 + sizeof(long long) * (size_t)n + 256;
+                         256 + sizeof(coral_stats*) * (size_t)n + 256 + sizeof(long long) * (size_t)n + 256 +
+                         sizeof(CUtensorMap) * 2 * (size_t)n + 256 + sizeof(int) * (size_t)n + 256;
     if (e == cudaSuccess) e = cudaMalloc(&b->dmem, bytes);
     if (e != cudaSuccess) { rc = bfail(b, e == cudaErrorMemoryAllocation ? CORAL_E_OOM : CORAL_E_CUDA, cudaGetErrorString(e)); break; }
     char* p = static_cast<char*>(b->dmem);
@@ -924,6 +937,8 @@ extern "C" int coral_batch_create(coral_substrate* const* worlds, int32_t n, cor
     b->d_part = reinterpret_cast<int*>(carve(sizeof(int) * (4 * (size_t)b->max_grid + 6 * (size_t)n)));
     b->d_rings = reinterpret_cast<coral_stats**>(carve(sizeof(coral_stats*) * (size_t)n));
     b->d_steps = reinterpret_cast<long long*>(carve(sizeof(long long) * (size_t)n));
+    b->d_tmaps = reinterpret_cast<CUtensorMap*>(carve(sizeof(CUtensorMap) * 2 * (size_t)n));   // 256-byte aligned
+    b->d_tma_ok = reinterpret_cast<int*>(carve(sizeof(int) * (size_t)n));
     std::vector<coral_stats*> rings(n);
     for (int i = 0; i < n; ++i) rings[i] = worlds[i]->ring;
     if ((e = cudaMemcpy(b->d_rings, rings.data(), sizeof(coral_stats*) * n, cudaMemcpyHostToDevice)) != cudaSuccess) {

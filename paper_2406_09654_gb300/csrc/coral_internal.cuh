@@ -122,6 +122,9 @@ struct BatchTable {
   const int* world_ctas2;
   coral_stats* const* rings;      // [n] stats rings
   long long* steps;               // [n] step index of each world (advanced by the stats kernel)
+  const CUtensorMap* tmaps;       // [2][n] TMA descriptors of the worlds' sensor planes (parity p:
+                                  // the buffer args[p][w] reads), written by the host before use
+  const int* tma_ok;              // [n] the world has descriptors (rows a multiple of 16 bytes)
 };
 
 // ---- Philox4x32-10 (Salmon et al., SC'11), written for the device -----------------------

@@ -515,8 +515,13 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16_batch(const
   __shared__ StepArgs sa;
   const int w = bt.cta_world1[blockIdx.x];
   copy_args_to_shared(&sa, &bt.args[parity * bt.n + w]);
+  // this world's TMA descriptor lives in global memory (written by the host): thread 0, which
+  // issues the copies, orders it for the tensor-map proxy before the first use
+  const CUtensorMap* tm = bt.tmaps + parity * bt.n + w;
+  const int use_tma = bt.tma_ok[w];
+  if (use_tma && threadIdx.x == 0) tc::fence_tensormap_acquire(tm);
   __syncthreads();
-  pass1_bf16_body<kH>(sa, nullptr, 0, blockIdx.x - bt.world_first1[w], bt.world_ctas1[w]);
+  pass1_bf16_body<kH>(sa, tm, use_tma, blockIdx.x - bt.world_first1[w], bt.world_ctas1[w]);
 }
 
 // A wait that must run out: nothing arrives on the barrier. Same bounded wait, error report
