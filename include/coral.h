@@ -244,7 +244,7 @@ int coral_launch_config(const coral_substrate* s, int32_t* grid_pass1, int32_t* 
  * per-step launch sequence replayed as a CUDA graph). All worlds: BF16 path, the same hidden
  * size, radiation off, a genome table loaded, the current CUDA device. The CTAs of each launch
  * are divided among the worlds in proportion to their sizes, at least one each (each CTA works
- * on one world; a launch asks for 16 times the CTAs of its launch shape, so that the block
+ * on one world; a launch asks for 32 times the CTAs of its launch shape, so that the block
  * scheduler evens out small and large worlds), and a world's cells are bit-identical to
  * stepping it alone. The batch has its own stream; before
  * each coral_batch_step it waits for work already enqueued on the worlds' streams, and the
@@ -262,7 +262,7 @@ int coral_batch_step(coral_batch* b, int32_t n_steps);
 int coral_batch_step_timed(coral_batch* b, int32_t n_steps, float* step_ms);
 /*
  * Autotuner: times trial_steps steps (after one warm-up) for each candidate launch shape —
- * pass-1 CTAs per SM in {2, 3, 4, 5} x pass-2 CTAs per SM in {1, 2, 3}, each times 16 as
+ * pass-1 CTAs per SM in {2, 3, 4, 5} x pass-2 CTAs per SM in {1, 2, 3}, each times 32 as
  * above — keeps the fastest and
  * restores every world's state and step index afterwards. choice: [3] = {pass-1 CTAs per SM,
  * pass-2 CTAs per SM, best step time in microseconds} (may be NULL). Synchronises.

@@ -700,8 +700,9 @@ const char* coral_last_error(const coral_substrate* s) { return s ? s->err.c_str
 // Batched stepping
 // ---------------------------------------------------------------------------------------------
 // Batched launches ask for this many times the CTAs per SM of their launch shape (see partition;
-// on the 256-world batch 4, 8 and 16 gave 11.7, 11.6 and 11.2 ms per step).
-constexpr int kOversubscribe = 16;
+// on the 256-world batch 4, 8, 16 and 32 gave 11.7, 11.6, 11.2 and 11.0 ms per step, and 32
+// 10.7 against 16's 10.9 ms once the batch had TMA halos).
+constexpr int kOversubscribe = 32;
 
 struct coral_batch {
   std::vector<coral_substrate*> worlds;
