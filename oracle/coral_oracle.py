@@ -50,8 +50,10 @@ numbered reading [R1]..[R16]; each function names the readings it follows. The r
 [R12] slots: hits in increasing cell order take the lowest free slots (count 0 after the
       step's physics); excess hits are skipped and counted.
 [R13] no death rule.
-[R14] decisions on floats are taken in float32 (the kernel's precision) on both sides;
-      ``margins`` report how close each decision was, so tests can see near-ties.
+[R14] decisions on floats (the maximal explore actuator, its sign, the winning explorer, the
+      takeover compare) are taken on the FP64 values; ``margins`` report how close each
+      decision was, so that tests can set aside the near-ties a lower-precision path may
+      decide the other way.
 """
 from __future__ import annotations
 
@@ -281,14 +283,13 @@ def invest_liquidate(E, I, a, p: Params):
 def explore_decision(z, a, I1, R, p: Params):
     """[R6] pick the maximal explore actuator; explore iff it is positive and I1 > 0.
     z, a: pre-activations and actuators. Returns (direction 0..3 or -1, amount, margin). The
-    decision compares float32 values [R14]; the margin is the smaller of (top1 - top2) and
-    |top1| of the pre-activations in FP64."""
+    decision compares the FP64 values [R14]; the margin is the smaller of (top1 - top2) and
+    |top1| of the pre-activations."""
     logits = z[:, 6:10]
-    l32 = logits.astype(np.float32)
-    k = np.argmax(l32, axis=1)                       # first maximum
-    m32 = l32[np.arange(len(z)), k]
+    k = np.argmax(logits, axis=1)                    # first maximum
+    zm = logits[np.arange(len(z)), k]
     m = a[np.arange(len(a)), 6 + k]
-    go = (m32 > 0) & (I1.astype(np.float32) > 0)
+    go = (zm > 0) & (I1 > 0)
     turn = np.asarray(EXPLORE_TURN)[k]
     Rv = R if p.rotation else np.zeros_like(R)
     d = np.where(go, (Rv + turn) % 4, -1)
@@ -348,7 +349,6 @@ def pass2(st: State, p1, cells, t, p: Params):
     I1 = p1["I1"][cells]
     # a7 exploration: incoming explorers, winner, takeover [R6]
     I2 = I1 - p1["amt"][cells]
-    best_x32 = np.full(m, -np.inf, np.float32)
     best_x = np.full(m, -np.inf)
     second_x = np.full(m, -np.inf)
     best_n = np.full(m, -1, np.int64)
@@ -359,14 +359,12 @@ def pass2(st: State, p1, cells, t, p: Params):
         xin = np.where(inc, p1["amt"][nb], 0.0)
         I2 = I2 + xin
         n_in += inc
-        x32 = xin.astype(np.float32)
-        win = inc & (x32 > best_x32)                 # strict: earlier direction keeps ties
+        win = inc & (xin > best_x)                   # strict: earlier direction keeps ties
         second_x = np.where(inc, np.where(win, np.maximum(second_x, best_x),
                                           np.maximum(second_x, xin)), second_x)
-        best_x32 = np.where(win, x32, best_x32)
         best_x = np.where(win, xin, best_x)
         best_n = np.where(win, nb, best_n)
-    take = (best_n >= 0) & (best_x32 > I1.astype(np.float32))
+    take = (best_n >= 0) & (best_x > I1)
     G2 = st.G[cells].copy()
     R2 = st.R[cells].copy()
     G2[take] = st.G[best_n[take]]

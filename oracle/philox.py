@@ -12,7 +12,8 @@ random numbers from Philox4x32-10 keyed by the run seed, with counter (cell, ste
 stream<<24 | sub, world).
 
 The word-size generic form below is pinned in tests against numpy's Philox4x64-10 (a
-library routine with the same round structure); the 4x32 constants are the published ones.
+library routine with the same round structure) and, for the 4x32 width used here, against the
+known-answer vectors the generator's authors publish with their Random123 library.
 """
 from __future__ import annotations
 
