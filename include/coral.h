@@ -279,6 +279,15 @@ int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* choice);
  */
 int coral_selftest_wait_timeout(void* cuda_stream, int32_t wait_us, int32_t* status_out);
 
+/*
+ * Known-answer test hook of the radiation's random numbers (reading R2: Philox4x32-10 of
+ * Salmon et al., SC'11, keyed by the run seed): evaluates, on the current device, the same
+ * Philox4x32-10 function the radiation kernels draw from. ctr: host uint32 [n][4] counters;
+ * key: host uint32 [n][2] keys; out: host uint32 [n][4] results. n in [1, 65536], else
+ * E_INVALID. Uses the legacy default stream; allocates a temporary device buffer; synchronises.
+ */
+int coral_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int32_t n);
+
 /* Waits for the stream and returns the first latched device-side error, if any. */
 int coral_sync(coral_substrate* s);
 

@@ -90,6 +90,7 @@ SIGNATURES = {
     "coral_batch_step_timed": (ctypes.c_int, [_VP, _I32, _VP]),
     "coral_batch_tune": (ctypes.c_int, [_VP, _I32, _VP]),
     "coral_bucket_noalloc_last_error": (ctypes.c_char_p, []),
+    "coral_philox4x32_10": (ctypes.c_int, [_VP, _VP, _VP, _I32]),
 }
 
 _lib = None
@@ -430,6 +431,18 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 evaluated on the device by the radiation kernels' function (test hook):
+    ctr uint32 [n][4], key uint32 [n][2] -> uint32 [n][4]."""
+    c = np.ascontiguousarray(ctr, np.uint32).reshape(-1, 4)
+    k = np.ascontiguousarray(key, np.uint32).reshape(-1, 2)
+    if len(c) != len(k):
+        raise ValueError("ctr and key must have the same number of rows")
+    out = np.empty_like(c)
+    _check(lib().coral_philox4x32_10(c.ctypes.data, k.ctypes.data, out.ctypes.data, len(c)))
+    return out
 
 
 def selftest_wait_timeout(wait_us=1000, stream=None):

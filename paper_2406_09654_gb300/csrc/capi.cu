@@ -687,6 +687,25 @@ int coral_selftest_wait_timeout(void* cuda_stream, int32_t wait_us, int32_t* sta
   return CORAL_OK;
 }
 
+int coral_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int32_t n) {
+  if (!ctr || !key || !out) return fail(nullptr, CORAL_E_INVALID, "NULL argument");
+  if (n < 1 || n > 65536) return fail(nullptr, CORAL_E_INVALID, "n must be in [1, 65536]");
+  void* d = nullptr;
+  const size_t b_ctr = 16 * (size_t)n, b_key = 8 * (size_t)n;
+  cudaError_t e = cudaMalloc(&d, 2 * b_ctr + b_key);
+  uint32_t* dc = static_cast<uint32_t*>(d);
+  uint32_t* dout = dc + 4 * (size_t)n;
+  uint32_t* dk = dout + 4 * (size_t)n;
+  if (e == cudaSuccess) e = cudaMemcpy(dc, ctr, b_ctr, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dk, key, b_key, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = launch_philox(dc, dk, dout, n, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out, dout, b_ctr, cudaMemcpyDeviceToHost);
+  if (d) cudaFree(d);
+  if (e != cudaSuccess) return fail(nullptr, e == cudaErrorMemoryAllocation ? CORAL_E_OOM : CORAL_E_CUDA,
+                                    std::string("philox: ") + cudaGetErrorString(e));
+  return CORAL_OK;
+}
+
 int coral_sync(coral_substrate* s) {
   if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
   return check_status(s);

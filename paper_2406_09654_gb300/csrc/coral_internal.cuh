@@ -237,6 +237,8 @@ cudaError_t launch_dense_pack(const GenomeArgs& g, const float* dense, int n, cu
 cudaError_t launch_bf16_pack(const GenomeArgs& g, const int32_t* slots, const int* n_dev,
                              int n_host, cudaStream_t st);
 cudaError_t launch_read_dense(const GenomeArgs& g, int slot, float* dst, cudaStream_t st);
+// ctr [n][4], key [n][2], out [n][4] device arrays (16- and 8-byte aligned)
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t st);
 cudaError_t launch_genome_distances(const float* genes, const int32_t* slots, int n, float* out, cudaStream_t st);
 cudaError_t launch_validate_state(const int32_t* G, const uint8_t* R, long long N, int cap,
                                   int* status, cudaStream_t st);

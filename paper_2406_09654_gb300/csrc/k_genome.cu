@@ -645,7 +645,20 @@ __global__ void k_genome_distances(const float* genes, const int32_t* slots, int
   out[pair] = 0.4f * (acc / (float)kGenes);
 }
 
+// Philox4x32-10 on the device for listed counters and keys: the same function the radiation
+// kernels draw from (known-answer test hook).
+__global__ void __launch_bounds__(256) k_philox(const uint4* ctr, const uint2* key, uint4* out, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = philox4x32_10(ctr[i], key[i].x, key[i].y);
+}
+
 }  // namespace
+
+cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t st) {
+  k_philox<<<(n + 255) / 256, 256, 0, st>>>(reinterpret_cast<const uint4*>(ctr), reinterpret_cast<const uint2*>(key),
+                                            reinterpret_cast<uint4*>(out), n);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_genome_distances(const float* genes, const int32_t* slots, int n, float* out, cudaStream_t st) {
   const long long pairs = (long long)n * n;
