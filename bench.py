@@ -499,7 +499,7 @@ def main():
                               "scaling": "weak", "vs_baseline": None,
                               "dtype": "bf16 network operands, f32 accumulation and state", "data": "synthetic",
                               "config": {"workload": f"cfg5: {WORKLOADS['cfg5']}", "requests": a.steps},
-                              "p50_step_ms": r["p50_step_ms"], "p99_step_ms": r["p99_step_ms"], "serving": r}))
+                              "p50_step_ms": r["p50_step_wall_ms"], "p99_step_ms": r["p99_step_wall_ms"], "serving": r}))
         return
     if a.workload == "cfg4":
         import torch

@@ -77,8 +77,9 @@ typedef struct coral_params {
   int32_t day_period;      /* day/night period T in steps; day = first half  (200) */
   int32_t rotation;        /* 1 = kernel ordered by each cell's rotation, 0 = always north */
   int32_t radiation_every; /* M: radiation after step t when (t+1) % M == 0; 0 = off */
-  uint32_t thr_mut;        /* mutation hit iff Philox word < thr_mut  (floor(p * 2^32)) */
-  uint32_t thr_merge;      /* merge hit iff Philox word < thr_merge */
+  double p_mut;            /* mutation probability per cell and radiation event, in [0, 1]; a
+                              cell is hit iff its Philox word < min(floor(p_mut * 2^32), 2^32 - 1) */
+  double p_merge;          /* merge probability per cell and radiation event, in [0, 1] (same rule) */
   float sigma_mut;         /* std of the Gaussian added to every gene by a mutation (0.05) */
   uint32_t world;          /* Philox counter word 3 (distinguishes independent worlds) */
   uint64_t seed;           /* Philox key */
@@ -264,7 +265,9 @@ int coral_batch_step_timed(coral_batch* b, int32_t n_steps, float* step_ms);
  * Autotuner: times trial_steps steps (after one warm-up) for each candidate launch shape —
  * pass-1 CTAs per SM in {2, 3, 4, 5} x pass-2 CTAs per SM in {1, 2, 3}, each times 32 as
  * above — keeps the fastest and
- * restores every world's state and step index afterwards. choice: [3] = {pass-1 CTAs per SM,
+ * restores every world's state, step index and stats ring afterwards (also after an error,
+ * which leaves the launch shape the batch had before the call; a failed save or restore copy
+ * returns E_CUDA). choice: [3] = {pass-1 CTAs per SM,
  * pass-2 CTAs per SM, best step time in microseconds} (may be NULL). Synchronises.
  */
 int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* choice);
@@ -302,7 +305,10 @@ const char* coral_last_error(const coral_substrate* s);
  * Same result as coral_read_perm (stable counting sort of cell ids by genome slot), on
  * caller-owned device buffers: G [n_cells] int32 in [0, capacity), counts [capacity] int32 and
  * perm [n_cells] int32 (outputs). Work is enqueued on cuda_stream (NULL = legacy default
- * stream); the call returns after enqueueing and allocates nothing.
+ * stream); the call returns after enqueueing and allocates nothing. G is not validated (the
+ * call returns before the device reads it): a key outside [0, capacity) is left out of counts
+ * (the counts of valid slots stay exact) and perm is still a permutation of the cells, but its
+ * order is then unspecified.
  * Limits: n_cells <= 1,048,576 and capacity <= 65,536, else CORAL_E_INVALID with a message in
  * coral_bucket_noalloc_last_error(). The scratch is one fixed 12.3 MiB device array per GPU
  * that loads the library, kept until the process exits, shared by every call: calls that

@@ -323,6 +323,7 @@ def pass1(st: State, nets: Nets, cells, p: Params):
     out["dir"] = np.full(n, -2, np.int64)
     out["C"] = np.full((4, n), np.nan)
     out["a"] = np.full((n, N_OUT), np.nan)
+    out["z"] = np.full((n, N_OUT), np.nan)
     E1, I1 = invest_liquidate(st.E[cells], st.I[cells], a, p)
     d, amt, margin = explore_decision(z, a, I1, st.R[cells], p)
     out["E1"][cells], out["I1"][cells] = E1, I1
@@ -330,6 +331,7 @@ def pass1(st: State, nets: Nets, cells, p: Params):
     out["S"][cells] = flow_denominator(st, cells)
     out["C"][:, cells] = com_activation(a).T
     out["a"][cells] = a
+    out["z"][cells] = z
     return out
 
 
@@ -350,18 +352,17 @@ def pass2(st: State, p1, cells, t, p: Params):
     # a7 exploration: incoming explorers, winner, takeover [R6]
     I2 = I1 - p1["amt"][cells]
     best_x = np.full(m, -np.inf)
-    second_x = np.full(m, -np.inf)
     best_n = np.full(m, -1, np.int64)
-    n_in = np.zeros(m, np.int64)
+    xs = np.full((4, m), -np.inf)            # incoming amount per direction (-inf: none)
+    Is = np.zeros((4, m))                    # I1 of the explorer it comes from
     for D, (dx, dy) in enumerate(DIRS):
         nb = neighbour(W, H, cells, dx, dy)
         inc = p1["dir"][nb] == (D + 2) % 4          # neighbour north of me exploring south...
         xin = np.where(inc, p1["amt"][nb], 0.0)
         I2 = I2 + xin
-        n_in += inc
+        xs[D] = np.where(inc, xin, -np.inf)
+        Is[D] = np.where(inc, p1["I1"][nb], 0.0)
         win = inc & (xin > best_x)                   # strict: earlier direction keeps ties
-        second_x = np.where(inc, np.where(win, np.maximum(second_x, best_x),
-                                          np.maximum(second_x, xin)), second_x)
         best_x = np.where(win, xin, best_x)
         best_n = np.where(win, nb, best_n)
     take = (best_n >= 0) & (best_x > I1)
@@ -369,11 +370,22 @@ def pass2(st: State, p1, cells, t, p: Params):
     R2 = st.R[cells].copy()
     G2[take] = st.G[best_n[take]]
     R2[take] = p1["dir"][best_n[take]]
-    bx = np.where(best_n >= 0, best_x, 0.0)
-    sx = np.where(n_in >= 2, second_x, 0.0)
-    scale = np.maximum(np.maximum(np.abs(bx), np.abs(I1)), 1e-30)
-    tmargin = np.where(best_n >= 0, np.abs(bx - I1) / scale, np.inf)
-    tmargin = np.minimum(tmargin, np.where(n_in >= 2, (bx - sx) / scale, np.inf))
+    # margins of the winner and takeover compares: relative to the compared amounts, and in
+    # units of the explore actuators (an amount x = k_exp m I1 moves by at most k_exp I1 per
+    # unit change of m); the smaller of the two
+    has = best_n >= 0
+    order = np.argsort(-xs, axis=0, kind="stable")
+    col = np.arange(m)
+    x1, x2 = xs[order[0], col], xs[order[1], col]
+    i1, i2 = Is[order[0], col], Is[order[1], col]
+    bx = np.where(has, x1, 0.0)
+    rel = np.maximum(np.maximum(np.abs(bx), np.abs(I1)), 1e-30)
+    tmargin = np.where(has, np.abs(bx - I1) / np.maximum(rel, p.k_exp * i1), np.inf)
+    two = np.isfinite(x2)
+    d12 = np.where(two, x1 - np.where(two, x2, 0.0), np.inf)
+    rel2 = np.maximum(np.abs(bx), 1e-30)
+    z2 = np.maximum(p.k_exp * (i1 + i2), 1e-30)
+    tmargin = np.minimum(tmargin, np.where(two, d12 / np.maximum(rel2, z2), np.inf))
     # a8 energy flow along infrastructure [R7]
     E1 = p1["E1"][cells]
     S = p1["S"][cells]
@@ -397,7 +409,7 @@ def step(st: State, nets: Nets, t: int, p: Params):
     new = State(st.width, st.height, o["E"], o["I"], o["C"], o["G"], o["R"])
     info = dict(stats=totals(new), n_explore=int(o["explore"].sum()),
                 n_takeover=int(o["take"].sum()), margin_explore=p1["margin"],
-                margin_target=o["tmargin"], dir=p1["dir"], amt=p1["amt"], a=p1["a"],
+                margin_target=o["tmargin"], dir=p1["dir"], amt=p1["amt"], a=p1["a"], z=p1["z"],
                 E1=p1["E1"], I1=p1["I1"], S=p1["S"])
     return new, info
 
@@ -412,6 +424,7 @@ def step_cells(st: State, nets: Nets, t: int, p: Params, cells):
     o["margin_explore"] = p1["margin"][cells]
     o["margin_explore_nb"] = np.min(
         [p1["margin"][nb] for nb in need[1:]] + [p1["margin"][cells]], axis=0)
+    o["pass1"] = p1
     return o
 
 

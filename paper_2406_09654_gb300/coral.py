@@ -7,7 +7,6 @@ Arrays may be numpy arrays (host memory) or CUDA torch tensors (device memory).
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 
 import numpy as np
@@ -35,8 +34,8 @@ class Params(ctypes.Structure):
         ("k_inv", ctypes.c_float), ("k_liq", ctypes.c_float), ("k_exp", ctypes.c_float),
         ("k_flow", ctypes.c_float), ("e_day", ctypes.c_float), ("e_night", ctypes.c_float),
         ("day_period", ctypes.c_int32), ("rotation", ctypes.c_int32),
-        ("radiation_every", ctypes.c_int32), ("thr_mut", ctypes.c_uint32),
-        ("thr_merge", ctypes.c_uint32), ("sigma_mut", ctypes.c_float),
+        ("radiation_every", ctypes.c_int32), ("p_mut", ctypes.c_double),
+        ("p_merge", ctypes.c_double), ("sigma_mut", ctypes.c_float),
         ("world", ctypes.c_uint32), ("seed", ctypes.c_uint64),
         ("fma_cutoff", ctypes.c_int32), ("max_mma_genomes", ctypes.c_int32),
     ]
@@ -117,11 +116,6 @@ def _check(rc, handle=None):
         raise CoralError(rc, msg.decode() if msg else "")
 
 
-def threshold(p: float) -> int:
-    """Radiation hit threshold: a hit is a 32-bit Philox word below floor(p * 2^32)."""
-    return min(int(math.floor(float(p) * 4294967296.0)), 0xFFFFFFFF)
-
-
 def default_params() -> Params:
     p = Params()
     _check(lib().coral_params_default(ctypes.byref(p)))
@@ -139,8 +133,8 @@ def params_from_world(world, path=FP32_PERCELL, **overrides) -> Params:
     p.day_period = int(ph["day_period"])
     p.rotation = int(ph["rotation"])
     p.radiation_every = int(ph.get("radiation_every", 0))
-    p.thr_mut = threshold(ph.get("p_mut", 0.0))
-    p.thr_merge = threshold(ph.get("p_merge", 0.0))
+    p.p_mut = float(ph.get("p_mut", 0.0))
+    p.p_merge = float(ph.get("p_merge", 0.0))
     p.seed = int(world.seed)
     for k, v in overrides.items():
         setattr(p, k, v)

@@ -1,5 +1,6 @@
 // C ABI of the substrate-step library: substrate lifetime, device memory ownership, loads and
 // reads, and the per-step launch sequence. Declarations and contracts: include/coral.h.
+#include <math.h>
 #include <stdio.h>
 #include <string.h>
 
@@ -99,6 +100,13 @@ void free_all(coral_substrate* s) {
   s->allocs.clear();
 }
 
+// Radiation hit threshold of a probability (reading R2): a cell is hit iff its 32-bit Philox
+// word is below floor(p * 2^32), capped at 2^32 - 1 (p * 2^32 is exact in double precision).
+uint32_t hit_threshold(double p) {
+  const double t = floor(p * 4294967296.0);
+  return t >= 4294967295.0 ? 0xFFFFFFFFu : (uint32_t)t;
+}
+
 bool valid_hidden(int h) { return h == 0 || h == 16 || h == 32 || h == 48 || h == 64; }
 
 StepArgs step_args(const coral_substrate* s) {
@@ -169,8 +177,8 @@ int coral_params_default(coral_params* p) {
   p->day_period = 200;
   p->rotation = 1;
   p->radiation_every = 0;
-  p->thr_mut = 0;
-  p->thr_merge = 0;
+  p->p_mut = 0.0;
+  p->p_merge = 0.0;
   p->sigma_mut = 0.05f;
   p->world = 0;
   p->seed = 0;
@@ -192,6 +200,8 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
     return fail(nullptr, CORAL_E_INVALID, "unknown path");
   if (p->day_period < 1) return fail(nullptr, CORAL_E_INVALID, "day_period must be >= 1");
   if (p->radiation_every < 0) return fail(nullptr, CORAL_E_INVALID, "radiation_every must be >= 0");
+  if (!(p->p_mut >= 0.0 && p->p_mut <= 1.0) || !(p->p_merge >= 0.0 && p->p_merge <= 1.0))
+    return fail(nullptr, CORAL_E_INVALID, "p_mut and p_merge must be in [0, 1]");
   if (p->path == CORAL_NET_BF16_GROUPED && (p->max_mma_genomes < 1 || p->max_mma_genomes > 4))
     return fail(nullptr, CORAL_E_INVALID, "max_mma_genomes must be in [1, 4]");
   coral_substrate* s = nullptr;
@@ -394,8 +404,8 @@ int enqueue_step(coral_substrate* s, cudaEvent_t* ev) {
     r.N = s->N;
     r.G = s->st[s->cur].G;
     r.g = s->g;
-    r.thr_mut = s->p.thr_mut;
-    r.thr_merge = s->p.thr_merge;
+    r.thr_mut = hit_threshold(s->p.p_mut);
+    r.thr_merge = hit_threshold(s->p.p_merge);
     r.sigma = s->p.sigma_mut;
     r.world = s->p.world;
     r.seed = s->p.seed;
@@ -1027,30 +1037,39 @@ extern "C" int coral_batch_step_timed(coral_batch* b, int32_t n_steps, float* st
 extern "C" int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* choice) {
   if (!b) return bfail(nullptr, CORAL_E_INVALID, "NULL batch");
   if (trial_steps < 1) return bfail(b, CORAL_E_INVALID, "trial_steps must be >= 1");
-  // save every world's current state and step index
+  const int cps1_0 = b->cps1, cps2_0 = b->cps2;
+  // save every world's current state, step index and stats ring
   std::vector<void*> saved(b->n, nullptr);
   std::vector<long long> t0(b->n);
   std::vector<int> c0(b->n);
+  auto release = [&]() {
+    for (void* q : saved)
+      if (q) cudaFree(q);
+  };
   for (int i = 0; i < b->n; ++i) {
     coral_substrate* s = b->worlds[i];
-    cudaStreamSynchronize(s->stream);
     t0[i] = s->t;
     c0[i] = s->cur;
-    const size_t bytes = (size_t)s->N * 29;
-    if (cudaMalloc(&saved[i], bytes) != cudaSuccess) {
-      for (void* q : saved) if (q) cudaFree(q);
-      cudaGetLastError();
-      return bfail(b, CORAL_E_OOM, "no memory to save the states for tuning");
-    }
+    const size_t bytes = (size_t)s->N * kStateBytesPerCell + sizeof(coral_stats) * kRing;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&saved[i], bytes);
     char* q = static_cast<char*>(saved[i]);
     const Planes& d = s->st[s->cur];
-    cudaMemcpy(q, d.E, (size_t)s->N * 24, cudaMemcpyDeviceToDevice);
-    cudaMemcpy(q + (size_t)s->N * 24, d.G, (size_t)s->N * 4, cudaMemcpyDeviceToDevice);
-    cudaMemcpy(q + (size_t)s->N * 28, d.R, (size_t)s->N, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(q, d.E, (size_t)s->N * 24, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(q + (size_t)s->N * 24, d.G, (size_t)s->N * 4, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(q + (size_t)s->N * 28, d.R, (size_t)s->N, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(q + (size_t)s->N * kStateBytesPerCell, s->ring, sizeof(coral_stats) * kRing, cudaMemcpyDeviceToDevice);
+    if (e != cudaSuccess) {
+      release();
+      cudaGetLastError();
+      return bfail(b, e == cudaErrorMemoryAllocation ? CORAL_E_OOM : CORAL_E_CUDA,
+                   std::string("saving the states for tuning: ") + cudaGetErrorString(e));
+    }
   }
   const int c1s[4] = {2, 3, 4, 5}, c2s[3] = {1, 2, 3};
   float best = 1e30f;
-  int b1 = b->cps1, b2 = b->cps2, rc = CORAL_OK;
+  int b1 = cps1_0, b2 = cps2_0, rc = CORAL_OK;
   std::vector<float> ms(trial_steps + 1);
   for (int i1 = 0; i1 < 4 && rc == CORAL_OK; ++i1)
     for (int i2 = 0; i2 < 3 && rc == CORAL_OK; ++i2) {
@@ -1066,21 +1085,34 @@ extern "C" int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* ch
         b2 = c2s[i2];
       }
     }
-  // restore
-  cudaStreamSynchronize(b->stream);
+  // restore the states, step indices and stats rings, also after an error
+  cudaError_t e = cudaStreamSynchronize(b->stream);
   for (int i = 0; i < b->n; ++i) {
     coral_substrate* s = b->worlds[i];
-    cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     s->cur = c0[i];
     s->t = t0[i];
     const char* q = static_cast<const char*>(saved[i]);
     const Planes& d = s->st[s->cur];
-    cudaMemcpy(d.E, q, (size_t)s->N * 24, cudaMemcpyDeviceToDevice);
-    cudaMemcpy(d.G, q + (size_t)s->N * 24, (size_t)s->N * 4, cudaMemcpyDeviceToDevice);
-    cudaMemcpy(d.R, q + (size_t)s->N * 28, (size_t)s->N, cudaMemcpyDeviceToDevice);
-    cudaFree(saved[i]);
+    if (e == cudaSuccess) e = cudaMemcpy(d.E, q, (size_t)s->N * 24, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d.G, q + (size_t)s->N * 24, (size_t)s->N * 4, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(d.R, q + (size_t)s->N * 28, (size_t)s->N, cudaMemcpyDeviceToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(s->ring, q + (size_t)s->N * kStateBytesPerCell, sizeof(coral_stats) * kRing, cudaMemcpyDeviceToDevice);
   }
-  if (rc != CORAL_OK) return rc;
+  release();
+  if (e != cudaSuccess && rc == CORAL_OK)
+    rc = bfail(b, CORAL_E_CUDA, std::string("restoring the states after tuning: ") + cudaGetErrorString(e));
+  if (rc != CORAL_OK) {
+    // back to the launch shape the batch had before tuning
+    b->cps1 = cps1_0;
+    b->cps2 = cps2_0;
+    const std::string keep = b->err;
+    batch_configure(b);
+    b->err = keep;
+    g_err = keep;
+    return rc;
+  }
   b->cps1 = b1;
   b->cps2 = b2;
   if ((rc = batch_configure(b)) != CORAL_OK) return rc;

@@ -97,7 +97,8 @@ class WorldServer:
         batch = None
         dirty = False
         step_lat = []                    # (batch step ms, resident worlds) per batched step
-        req_step_ms = []                 # one entry per request-step: the step time it saw
+        req_step_ms = []                 # one entry per request-step: the device time of its step
+        req_step_wall = []               # one entry per request-step: wall time of its chunk / steps
         completed = []
         work = 0
         t0 = self.clock()
@@ -126,6 +127,7 @@ class WorldServer:
                 if pending:                                   # idle until the next arrival
                     self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
                 continue
+            chunk_t0 = self.clock()      # the chunk's wall time covers rebuilds, steps, reads
             if dirty or batch is None:
                 if batch is not None:
                     self.backend.free_batch(batch)
@@ -137,6 +139,7 @@ class WorldServer:
                 step_lat.append((float(m), len(active)))
                 req_step_ms.extend([float(m)] * len(active))
             work += n * sum(v[0].world.n_cells for v in active.values())
+            resident = len(active)
             done = [rid for rid, v in active.items() if v[2] - n <= 0]
             for v in active.values():
                 v[2] -= n
@@ -150,17 +153,27 @@ class WorldServer:
                     used -= need
                     completed.append(Completed(rid, r.arrival, adm, self.clock() - t0, r.steps,
                                                r.world.n_cells, res))
+            req_step_wall.extend([1e3 * (self.clock() - chunk_t0) / n] * (resident * n))
         if batch is not None:
             self.backend.free_batch(batch)
         makespan = self.clock() - t0
         lat = np.array(req_step_ms) if req_step_ms else np.zeros(1)
+        wall = np.array(req_step_wall) if req_step_wall else np.zeros(1)
         served = [c for c in completed if c.admitted >= 0]
+        # per request: wall time from admission to its result, per step
+        per_req = [1e3 * (c.finished - c.admitted) / c.steps for c in served if c.steps > 0] or [0.0]
         report = {
             "requests": len(completed), "served": len(served),
             "rejected": len(completed) - len(served),
             "makespan_s": makespan, "cell_updates": work,
             "cell_updates_per_s": work / makespan if makespan > 0 else 0.0,
-            "p50_step_ms": float(np.percentile(lat, 50)), "p99_step_ms": float(np.percentile(lat, 99)),
+            # device time of the batched step each request-step ran in
+            "p50_step_device_ms": float(np.percentile(lat, 50)), "p99_step_device_ms": float(np.percentile(lat, 99)),
+            # wall time per step of the chunk each request-step ran in: batch rebuilds on admission
+            # and completion, the steps, and the read-back of finished worlds included
+            "p50_step_wall_ms": float(np.percentile(wall, 50)), "p99_step_wall_ms": float(np.percentile(wall, 99)),
+            "p50_request_ms_per_step": float(np.percentile(per_req, 50)),
+            "p99_request_ms_per_step": float(np.percentile(per_req, 99)),
             "batched_steps": len(step_lat),
             "mean_resident_worlds": float(np.mean([k for _, k in step_lat])) if step_lat else 0.0,
             "p50_queue_s": float(np.percentile([c.admitted - c.arrival for c in served], 50)) if served else 0.0,

@@ -64,10 +64,16 @@ def test_invalid_arguments_fail_before_any_device_work(lib):
     assert b"NULL" in lib.coral_last_error(None)
 
 
-def test_thresholds():
+def test_radiation_probabilities_are_validated(lib):
+    """p_mut and p_merge are probabilities: the library turns them into Philox thresholds and
+    refuses values outside [0, 1] (checked before any device work)."""
     from paper_2406_09654_gb300 import coral
-    assert coral.threshold(0) == 0 and coral.threshold(1.0) == 0xFFFFFFFF
-    assert coral.threshold(1e-4) == 429496
+    for field, bad in (("p_mut", -0.1), ("p_mut", 1.5), ("p_merge", float("nan")), ("p_merge", 2.0)):
+        p = coral.default_params()
+        setattr(p, field, bad)
+        with pytest.raises(coral.CoralError) as e:
+            coral.Substrate(p, 8, 8, 4)
+        assert e.value.code == coral.E_INVALID and "p_mut and p_merge" in str(e.value)
 
 
 def test_selftest_rejects_bad_arguments(lib):

@@ -90,3 +90,35 @@ def test_batch_rejects_mixed_configurations():
     finally:
         for s in (s1, s2, s3):
             s.close()
+
+
+def test_batched_worlds_match_oracle():
+    """Two worlds inside a batch of five, one oracle-forced step: both sides start from the
+    state the oracle reached after one step and step t = 1 (the other worlds run their own
+    states alongside)."""
+    from oracle import coral_oracle as O
+    from parity import check_bf16_step, oracle_setup, round32, state_arrays
+    ws = mixed_worlds(3, seed=9) + [worlds.make_world(width=96, height=64, n_genomes=7, hidden=32, net="cppn", seed=21),
+                                    worlds.make_world(width=130, height=70, n_genomes=9, hidden=32, net="cppn", seed=22,
+                                                      random_rotation=True)]
+    subs = [coral.substrate_for_world(w, coral.BF16_GROUPED) for w in ws]
+    try:
+        starts = []
+        for w, s in zip(ws[3:], subs[3:]):
+            st, nets, gen, p = oracle_setup(w)
+            st = round32(O.step(round32(st), nets, 0, p)[0])
+            s.load_state(*state_arrays(st))
+            starts.append(st)
+        for s in subs:
+            s.set_step(1)
+        with coral.Batch(subs) as b:
+            b.step(1)
+        for w, s, st in zip(ws[3:], subs[3:], starts):
+            _, nets, _, p = oracle_setup(w)
+            _, nets_b, _, p_b = oracle_setup(w, net_precision="bf16")
+            _, errs, frac = check_bf16_step(s.read_channels(), st, 1, nets, p, nets_b, p_b)
+            print(w.width, w.height, errs, "band", round(frac, 4))
+            assert frac <= 0.05
+    finally:
+        for s in subs:
+            s.close()

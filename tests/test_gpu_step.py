@@ -21,9 +21,10 @@ def _lib():
     coral.lib()
 
 
-def forced_steps(world, path, steps, tol, tau, t0=0, **pkw):
+def forced_steps(world, path, steps, tol, tau, t0=0, max_band_frac=0.05, **pkw):
     """Oracle-forced parity: at every step both sides start from the oracle's state (rounded
-    to float32); the GPU's next state is compared with the oracle's next state."""
+    to float32); the GPU's next state is compared with the oracle's next state. The cells set
+    aside by the decision band may be at most max_band_frac of all compared cells."""
     st, nets, gen, p = oracle_setup(world, **pkw)
     sub = coral.substrate_for_world(world, path)
     worst = {}
@@ -36,7 +37,7 @@ def forced_steps(world, path, steps, tol, tau, t0=0, **pkw):
             sub.step(1)
             g = sub.read_channels()
             new, info = O.step(st, nets, t, p)
-            mask = band_mask(st, info, tau)
+            mask = band_mask(st, info, tau, p.rotation)
             banded += int(mask.sum())
             errs, bad_G, bad_R = compare_step(g, new, mask, tol)
             assert bad_G == 0 and bad_R == 0, (t, bad_G, bad_R)
@@ -46,6 +47,7 @@ def forced_steps(world, path, steps, tol, tau, t0=0, **pkw):
             st = round32(new)
     finally:
         sub.close()
+    assert banded <= max_band_frac * steps * world.n_cells, banded
     return worst, banded
 
 
@@ -70,7 +72,7 @@ def test_cfg1_fp32_free_running_100_steps():
         for t in range(100):
             new, info = O.step(st, nets, t, p)
             sub.step(1)
-            mask = band_mask(st, info, FREE_TAU)
+            mask = band_mask(st, info, FREE_TAU, p.rotation)
             if mask.any():
                 first_band = t
                 break
@@ -91,7 +93,8 @@ def test_cfg1_fp32_free_running_100_steps():
 def test_fp32_shapes_and_hidden_sizes(W, H, n, hidden, rot):
     w = worlds.make_world(width=W, height=H, n_genomes=n, hidden=hidden, net="cppn" if hidden else "direct",
                           seed=W * 7 + H, random_rotation=True, rotation=rot)
-    forced_steps(w, coral.FP32_PERCELL, 4, FP32_TOL, FP32_TAU, t0=97)
+    # on the 3x3 and 3x5 tori a single near-tie is 7-11% of the grid
+    forced_steps(w, coral.FP32_PERCELL, 4, FP32_TOL, FP32_TAU, t0=97, max_band_frac=0.05 if W * H > 15 else 0.25)
 
 
 def test_fp32_day_night_boundary_and_stats():
@@ -109,7 +112,7 @@ def test_fp32_day_night_boundary_and_stats():
             tot = O.totals(new)
             assert s["step"] == t
             assert s["sum_E"] == pytest.approx(tot["E"], rel=2e-6)
-            mask = band_mask(st, info, FP32_TAU)
+            mask = band_mask(st, info, FP32_TAU, p.rotation)
             if not mask.any():
                 assert s["sum_I"] == pytest.approx(tot["I"], rel=2e-6)
                 assert s["n_explore"] == info["n_explore"] and s["n_takeover"] == info["n_takeover"]
