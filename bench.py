@@ -44,8 +44,7 @@ WORKLOADS = {
             "150 GB device-memory budget, continuous batching",
 }
 STATE_BYTES = 29          # E, I, C0..C3 float32 + G int32 + R uint8 per cell
-P1_BYTES = 45             # pass 1 reads the state (29 B) and writes C' (16 B)
-P2_BYTES = 13             # pass 2 writes E', I' (float32), G' (int32), R' (uint8)
+STEP_BYTES = 2 * STATE_BYTES   # algorithmic HBM bytes per cell-update: state read once, written once
 
 
 def parse():
@@ -62,7 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batched-steps", type=int, default=10, help="steps of the 256-world batch (0 = skip)")
-    ap.add_argument("--serving-requests", type=int, default=16, help="requests of the serving run (0 = skip)")
+    ap.add_argument("--serving-requests", type=int, default=200, help="requests of the serving run (0 = skip)")
+    ap.add_argument("--serving-slots", type=int, default=64, help="batch slots of the serving run")
     return ap.parse_args()
 
 
@@ -160,11 +160,13 @@ class ClockSampler:
 # ----------------------------------------------------------------------------- peaks, traffic
 
 def measured_peaks():
+    """(HBM GB/s, BF16 TFLOP/s burst, BF16 TFLOP/s sustained, max SM MHz, 'measured'|'fallback')."""
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         d = json.load(open(p))
-        return d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("sm_max_mhz", 2070.0), "measured"
-    return 6800.0, 1900.0, 2070.0, "fallback"
+        return (d.get("hbm_gbs", 6800.0), d.get("bf16_tflops", 1900.0), d.get("bf16_tflops_sustained", 1700.0),
+                d.get("sm_max_mhz", 2070.0), "measured")
+    return 6800.0, 1900.0, 1700.0, 2070.0, "fallback"
 
 
 # translation unit of each profiled kernel; every header and the build flags count for all
@@ -215,51 +217,120 @@ def recorded_traffic(kernel, workload):
 # ----------------------------------------------------------------------------- oracle baseline
 
 CPU_SNIPPET = r"""
-import sys, time, json, numpy as np
+import json, multiprocessing as mp, os, sys, time
+import numpy as np
 sys.path.insert(0, {root!r})
 from oracle import coral_oracle as O
 from paper_2406_09654_gb300 import worlds
-w = worlds.make_world({workload!r}, seed={seed})
+cfg = json.loads({cfg!r})
+w = worlds.make_world(cfg["workload"], seed=cfg["seed"])
 st = O.State.from_world(w)
 p = O.Params.from_world(w)
 nets = O.nets_from_genomes(O.Genomes.from_genes(w.genes, w.n_genomes), w.hidden) if w.genes is not None \
     else O.Nets.from_dense(w.dense, w.hidden)
-rows, budget, max_bands = {rows}, {budget}, {max_bands}
-times, cells = [], []
-y = 0
-while len(times) < max_bands and (sum(times) < budget or len(times) < {min_bands}):
-    band = np.arange(y * w.width, min(w.height, y + rows) * w.width)
+rows = cfg["rows"]
+
+
+def band(y):
+    # pass 1 on the band of `rows` full rows and its neighbours, pass 2 on the band
+    cells = np.arange(y * w.width, min(w.height, y + rows) * w.width)
     t0 = time.perf_counter()
-    O.step_cells(st, nets, 0, p, band)
-    times.append(time.perf_counter() - t0)
-    cells.append(len(band))
+    O.step_cells(st, nets, 0, p, cells)
+    return time.perf_counter() - t0, len(cells)
+
+
+def bands(ys):
+    return [band(y % w.height) for y in ys]
+
+
+out = {{}}
+# one thread: successive bands until the budget (at least min_bands)
+times, cells, y = [], [], 0
+while len(times) < cfg["max_bands"] and (sum(times) < cfg["budget"] or len(times) < cfg["min_bands"]):
+    t, c = band(y)
+    times.append(t)
+    cells.append(c)
     y = (y + rows) % w.height
-print(json.dumps(dict(times=times, cells=cells)))
+out["single"] = dict(times=times, cells=cells)
+# all cores: one process per core (forked after the world is built; no GPU in this process),
+# each working through its own bands; the wall time of the whole pool is measured
+workers = cfg["workers"]
+if workers > 1 and cfg["parallel_rounds"] > 0:
+    per = max(1, int(round(cfg["parallel_budget"] / max(np.mean(times), 1e-6))))
+    if cfg["rounds_per_step"]:
+        per = 1
+    ctx = mp.get_context("fork")
+    with ctx.Pool(workers) as pool:
+        pool.map(abs, range(workers))                     # workers started before timing
+        rounds = []
+        for r in range(cfg["parallel_rounds"]):
+            jobs = [[rows * (r * workers * per + k * per + i) for i in range(per)] for k in range(workers)]
+            t0 = time.perf_counter()
+            res = pool.map(bands, jobs)
+            wall = time.perf_counter() - t0
+            rounds.append(dict(wall=wall, cells=int(sum(c for part in res for _, c in part))))
+    out["parallel"] = dict(workers=workers, bands_per_worker=per, rounds=rounds)
+print(json.dumps(out))
 """
 
 
-def oracle_bands(workload, seed, budget, min_bands=1, max_bands=10**6, rows=16):
-    """Runs the FP64 oracle as it stands, one thread, on successive bands of `rows` full rows of
-    the same world (pass 1 on the band and its neighbours, pass 2 on the band) until about
-    `budget` seconds, in a fresh process; returns per-band (seconds, cells)."""
+def cpu_info():
+    """(usable host cores, CPU model name)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    model = "unknown"
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return cores, model
+
+
+def oracle_run(workload, seed, budget=0.0, min_bands=1, max_bands=10**6, rows=16, workers=1,
+               parallel_rounds=0, parallel_budget=0.0, rounds_per_step=False):
+    """Runs the FP64 oracle as it stands in a fresh process (OpenMP/BLAS threads pinned to 1),
+    on bands of `rows` full rows of the same world (pass 1 on the band and its neighbours, pass 2
+    on the band): first on one thread until about `budget` seconds, then, with workers > 1, on a
+    pool of that many processes (parallel_rounds rounds of about parallel_budget seconds, or one
+    band per worker per round). Returns the parsed per-band and per-round figures."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = CPU_SNIPPET.format(root=ROOT, workload=workload, seed=seed, rows=rows, budget=budget,
-                              min_bands=min_bands, max_bands=max_bands)
+    cfg = json.dumps(dict(workload=workload, seed=seed, budget=budget, min_bands=min_bands, max_bands=max_bands,
+                          rows=rows, workers=workers, parallel_rounds=parallel_rounds,
+                          parallel_budget=parallel_budget, rounds_per_step=rounds_per_step))
+    code = CPU_SNIPPET.format(root=ROOT, cfg=cfg)
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-400:])
-    d = json.loads(r.stdout.strip().splitlines()[-1])
-    return d["times"], d["cells"]
+    return json.loads(r.stdout.strip().splitlines()[-1])
 
 
 def cpu_baseline(workload, seed, budget, rows=16):
+    """The oracle on one thread and on every host core, same world, bounded samples."""
+    cores, model = cpu_info()
     try:
-        times, cells = oracle_bands(workload, seed, budget, rows=rows)
+        d = oracle_run(workload, seed, budget=budget, rows=rows, workers=cores, parallel_rounds=1,
+                       parallel_budget=budget)
     except RuntimeError as e:
-        return {"value": None, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
-    return {"value": sum(cells) / sum(times), "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
-            "sample": f"{len(times)} bands of {rows} full rows ({sum(cells)} cells) of the same world, "
-                      f"step 0, {sum(times):.1f} s, 1 thread (FP64 numpy oracle)"}
+        return {"value": None, "unit": "cell-updates/s", "cores": cores, "kind": "oracle", "sample": f"failed: {e}"}
+    single = d["single"]
+    v1 = sum(single["cells"]) / sum(single["times"])
+    res = {"value": v1, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "cpu_model": model, "nproc": cores,
+           "sample": f"{len(single['times'])} bands of {rows} full rows ({sum(single['cells'])} cells) of the same "
+                     f"world, step 0, {sum(single['times']):.1f} s, 1 thread (FP64 numpy oracle)"}
+    if "parallel" in d:
+        rd = d["parallel"]["rounds"][0]
+        res.update(value=rd["cells"] / rd["wall"], cores=cores,
+                   sample=f"{cores} processes (one per host core) x {d['parallel']['bands_per_worker']} bands of "
+                          f"{rows} full rows each ({rd['cells']} cells) of the same world, step 0, wall "
+                          f"{rd['wall']:.1f} s (FP64 numpy oracle, one thread per process)",
+                   single_thread={"value": v1, "cores": 1, "sample": res["sample"]})
+    return res
 
 
 # ----------------------------------------------------------------------------- batched worlds
@@ -290,12 +361,15 @@ def run_batched(n_worlds, steps, warmup, seed, tune=True):
 
 # ----------------------------------------------------------------------------- serving
 
-def run_serving(n_requests, seed, budget_gb=150.0, rate=200.0):
-    """cfg5: continuous-batching world server over seeded Poisson requests."""
+def run_serving(n_requests, seed, budget_gb=150.0, rate=200.0, slots=64):
+    """cfg5: continuous-batching world server over seeded Poisson requests (worlds built on
+    host threads as they queue), at most `slots` worlds per batch."""
     from paper_2406_09654_gb300 import serving, worlds
-    reqs = serving.poisson_requests(n_requests, rate, worlds.request_world_factory((128, 4096), (8, 1024), 32),
+    reqs = serving.poisson_requests(n_requests, rate,
+                                    worlds.request_world_factory((128, 4096), (8, 1024), 32, lazy=True),
                                     (10, 1000), seed=seed)
-    srv = serving.WorldServer(serving.CoralBackend(), budget_bytes=int(budget_gb * (1 << 30)), chunk_steps=8)
+    srv = serving.WorldServer(serving.CoralBackend(), budget_bytes=int(budget_gb * (1 << 30)), chunk_steps=8,
+                              max_worlds=slots)
     _, rep = srv.run(reqs)
     rep["requests_generated"] = n_requests
     rep["rate_per_s"] = rate
@@ -349,28 +423,29 @@ def run_coral(a, rank, world_size, local):
     # dominant kernel: pass 1 (the network)
     p1_ms = float(np.mean(stage_ms[:, 0]))
     p2_ms = float(np.mean(stage_ms[:, 1]))
-    hbm, bf16_tf, sm_max, peak_kind = measured_peaks()
+    hbm, bf16_tf, bf16_sus, sm_max, peak_kind = measured_peaks()
     H = w.hidden
     macs = (54 * H + 10 * H) if H else 540
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     if path == "bf16":
-        # The tightest bound of this kernel is the special-function unit: every cell needs H
-        # hidden tanh, 10 output tanh and 4 sigmoids (H + 14 evaluations), at 16 results per
-        # clock per SM; its HBM share (45 B/cell) is reported beside it.
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
-        sfu_peak = sms * 16 * sm_max * 1e6 / 1e12
-        trans = (H if H else 0) + 10 + 4
-        achieved = trans * N / (p1_ms / 1e3) / 1e12
-        hbm_ach = P1_BYTES * N / (p1_ms / 1e3) / 1e9
-        roof = {"bound": "alu", "achieved": achieved, "peak": sfu_peak,
-                "unit": "Tops/s (tanh/sigmoid evaluations on the special-function unit)",
-                "frac": achieved / sfu_peak,
-                "peak_kind": "derived: SMs x 16 special-function results/clk x max SM clock "
-                             "(a tanh.approx probe measured 4.76 Tops/s = 95% of it)",
+        # The step's algorithmic HBM bytes per cell-update (state read once and written once,
+        # 58 B) over the dominant kernel's time, against the measured copy bandwidth; beside it
+        # the same kernel's tensor-core FLOPs (against the sustained BF16 peak) and its
+        # tanh/sigmoid evaluations (H hidden, 10 output, 4 sigmoids; against the measured
+        # special-function rate).
+        ach = STEP_BYTES * N / (p1_ms / 1e3) / 1e9
+        sfu_peak = coral.measure_sfu_rate(stream) / 1e9
+        evals = (H + 14) * N / (p1_ms / 1e3) / 1e9
+        tflops = 2 * macs * N / (p1_ms / 1e3) / 1e12
+        roof = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "peak_kind": f"{peak_kind}: MEASURED_PEAKS.json hbm_gbs (copy)",
                 "traffic": recorded_traffic("pass1_bf16", a.workload), "kernel": "pass1_bf16",
-                "hbm": {"achieved": hbm_ach, "peak": hbm, "unit": "GB/s", "frac": hbm_ach / hbm,
-                        "peak_kind": peak_kind, "algorithmic_bytes_per_cell": P1_BYTES}}
+                "algorithmic_bytes_per_cell": STEP_BYTES, "cells_per_launch": N,
+                "tensor": {"achieved": tflops, "peak": bf16_sus, "unit": "TFLOP/s", "frac": tflops / bf16_sus,
+                           "flops_per_cell": 2 * macs, "peak_kind": f"{peak_kind}: bf16_tflops_sustained"},
+                "sfu": {"achieved": evals, "peak": sfu_peak, "unit": "Geval/s", "frac": evals / sfu_peak,
+                        "evals_per_cell": H + 14, "peak_kind": "measured: coral_measure_sfu_rate (tanh.approx.f32)"}}
     else:
-        sms = torch.cuda.get_device_properties(local).multi_processor_count
         peak = sms * 128 * 2 * sm_max * 1e6 / 1e12
         achieved = 2 * macs * N / (p1_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -434,7 +509,7 @@ def run_coral(a, rank, world_size, local):
     if path == "bf16" and a.batched_steps > 0:
         batched = run_batched(256, a.batched_steps, 2, seed=rank)
     if path == "bf16" and a.serving_requests > 0:
-        served = run_serving(a.serving_requests, seed=rank)
+        served = run_serving(a.serving_requests, seed=rank, slots=a.serving_slots)
 
     if rank != 0:
         return None
@@ -472,18 +547,24 @@ def main():
     if a.impl == "reference":
         if rank == 0:
             wl = a.workload if a.workload in ("cfg1", "cfg2", "cfg3") else "cfg3"
-            times, cells = oracle_bands(wl, 0, 0.0, min_bands=a.warmup + a.steps, max_bands=a.warmup + a.steps)
-            t, c = times[a.warmup:], cells[a.warmup:]
-            v = sum(c) / sum(t)
-            sample = (f"each step: one band of 16 full rows ({c[0]} cells) of the {wl} world through the FP64 "
-                      f"numpy oracle, 1 thread")
+            cores, model = cpu_info()
+            # each step: one band of 16 full rows per host core, all in parallel
+            d = oracle_run(wl, 0, budget=0.0, min_bands=1, max_bands=1, workers=max(cores, 2),
+                           parallel_rounds=a.warmup + a.steps, rounds_per_step=True)
+            rounds = d["parallel"]["rounds"][a.warmup:]
+            wall = sum(r["wall"] for r in rounds)
+            v = sum(r["cells"] for r in rounds) / wall
+            sample = (f"each step: one band of 16 full rows ({rounds[0]['cells'] // max(cores, 2)} cells) of the {wl} "
+                      f"world per process, {max(cores, 2)} processes on {cores} host cores ({model}), FP64 numpy "
+                      f"oracle, one thread per process")
             print(json.dumps({
                 "impl": "reference", "metric": METRIC, "value": v, "unit": "cell-updates/s",
                 "n_gpus": world_size, "steps": a.steps, "warmup": a.warmup,
-                "ms_per_step": 1e3 * sum(t) / len(t), "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": 1e3 * wall / len(rounds), "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": f"{wl}: {WORKLOADS[wl]}", "path": "oracle"},
-                "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+                "cpu_baseline": {"value": v, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
+                                 "sample": sample, "cpu_model": model},
                 "e2e": {"value": v, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             }))
         return
@@ -492,7 +573,7 @@ def main():
         torch.cuda.set_device(local)
         from paper_2406_09654_gb300 import build
         build.build()
-        r = run_serving(a.steps, seed=rank)
+        r = run_serving(a.steps, seed=rank, slots=a.serving_slots)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": r["cell_updates_per_s"], "unit": "cell-updates/s",
                               "n_gpus": world_size, "steps": a.steps, "warmup": 0, "higher_is_better": True,

@@ -291,6 +291,15 @@ int coral_selftest_wait_timeout(void* cuda_stream, int32_t wait_us, int32_t* sta
  */
 int coral_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int32_t n);
 
+/*
+ * Measurement hook (library infrastructure; the paper has no counterpart): the throughput of
+ * the special-function unit for tanh.approx.f32, the instruction the BF16 path's hidden and
+ * output activations run on, measured on the current device with eight independent chains
+ * per thread over 8 CTAs of 256 threads per SM. *evals_per_s receives evaluations per second.
+ * cuda_stream: NULL = legacy default stream. Allocates a small device buffer; synchronises.
+ */
+int coral_measure_sfu_rate(void* cuda_stream, double* evals_per_s);
+
 /* Waits for the stream and returns the first latched device-side error, if any. */
 int coral_sync(coral_substrate* s);
 

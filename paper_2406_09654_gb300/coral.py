@@ -90,6 +90,7 @@ SIGNATURES = {
     "coral_batch_tune": (ctypes.c_int, [_VP, _I32, _VP]),
     "coral_bucket_noalloc_last_error": (ctypes.c_char_p, []),
     "coral_philox4x32_10": (ctypes.c_int, [_VP, _VP, _VP, _I32]),
+    "coral_measure_sfu_rate": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -437,6 +438,14 @@ def philox4x32_10(ctr, key):
     out = np.empty_like(c)
     _check(lib().coral_philox4x32_10(c.ctypes.data, k.ctypes.data, out.ctypes.data, len(c)))
     return out
+
+
+def measure_sfu_rate(stream=None) -> float:
+    """tanh.approx.f32 evaluations per second of the current device (measurement hook)."""
+    v = ctypes.c_double(0.0)
+    sp = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check(lib().coral_measure_sfu_rate(sp, ctypes.byref(v)))
+    return v.value
 
 
 def selftest_wait_timeout(wait_us=1000, stream=None):

@@ -716,6 +716,33 @@ int coral_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out,
   return CORAL_OK;
 }
 
+int coral_measure_sfu_rate(void* cuda_stream, double* evals_per_s) {
+  if (!evals_per_s) return fail(nullptr, CORAL_E_INVALID, "NULL argument");
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(nullptr, CORAL_E_CUDA, "device query failed");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+  const int blocks = 8 * sms, iters = 4096;
+  float* sink = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.0f;
+  cudaError_t e = cudaMalloc(&sink, sizeof(float) * blocks);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = launch_sfu_probe(blocks, iters, sink, st);              // warm-up
+  if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+  if (e == cudaSuccess) e = launch_sfu_probe(blocks, iters, sink, st);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (sink) cudaFree(sink);
+  if (e != cudaSuccess) return fail(nullptr, CORAL_E_CUDA, std::string("sfu probe: ") + cudaGetErrorString(e));
+  *evals_per_s = (double)blocks * 256.0 * 8.0 * iters / (ms * 1e-3);
+  return CORAL_OK;
+}
+
 int coral_sync(coral_substrate* s) {
   if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
   return check_status(s);

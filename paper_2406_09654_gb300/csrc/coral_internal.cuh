@@ -216,6 +216,8 @@ cudaError_t launch_pass2_batch(const BatchTable& b, int parity, int grid, cudaSt
 cudaError_t launch_stats_batch(const BatchTable& b, cudaStream_t st);
 int pass1_fp32_grid(int sms);
 cudaError_t launch_selftest_wait(long long max_cycles, int* status, cudaStream_t st);
+// blocks x 256 threads, each 8 x iters tanh.approx.f32 evaluations; sink: [blocks] floats
+cudaError_t launch_sfu_probe(int blocks, int iters, float* sink, cudaStream_t st);
 int pass1_bf16_grid(int sms);
 int pass2_grid(int sms);
 size_t pass1_bf16_smem();

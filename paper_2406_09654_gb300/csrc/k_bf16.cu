@@ -552,7 +552,29 @@ __global__ void __launch_bounds__(128) k_selftest_wait(long long max_cycles, int
   }
 }
 
+// Special-function unit throughput probe: eight independent tanh.approx.f32 chains per thread
+// (the instruction the hidden and output activations use); sink is written only if the chains
+// end on an impossible value, which keeps them live.
+__global__ void __launch_bounds__(256) k_sfu_probe(int iters, float* sink) {
+  float v[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) v[k] = 0.25f + 1e-3f * (float)(threadIdx.x + 37 * k);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = tc::tanh_approx(v[k]);
+  }
+  float s = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += v[k];
+  if (s == 12345.5f) sink[blockIdx.x] = s;
+}
+
 }  // namespace
+
+cudaError_t launch_sfu_probe(int blocks, int iters, float* sink, cudaStream_t st) {
+  k_sfu_probe<<<blocks, 256, 0, st>>>(iters, sink);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_selftest_wait(long long max_cycles, int* status, cudaStream_t st) {
   k_selftest_wait<<<1, 128, 0, st>>>(max_cycles, status);

@@ -2,7 +2,8 @@
 
 A request asks for one world (its seeded state and genome table) to be stepped a given number
 of times. Requests arrive over time; the server admits them in arrival order as soon as the
-memory they need fits in the budget, keeps every admitted world resident on the device, and
+memory they need fits in the budget and a batch slot is free, keeps every admitted world
+resident on the device, and
 steps all resident worlds together: one batched launch per pass over every world (the
 library's coral_batch_*), so a request that arrives while others run joins the next step and
 its work overlaps theirs on the device. A world that has done its steps is read back and freed,
@@ -51,14 +52,26 @@ class Completed:
 
 
 class CoralBackend:
-    """Real device backend: substrates and batches of the CUDA library."""
+    """Real device backend: substrates and batches of the CUDA library. Worlds given lazily
+    (with a ``materialize`` method) are built on a host thread pool as soon as they are queued,
+    so that building them overlaps the device's steps."""
 
-    def __init__(self, path=None):
+    def __init__(self, path=None, build_threads: int = 4):
+        from concurrent.futures import ThreadPoolExecutor
         from . import coral
         self.coral = coral
         self.path = coral.BF16_GROUPED if path is None else path
+        self.pool = ThreadPoolExecutor(max_workers=build_threads)
+        self.futures = {}
+
+    def prepare(self, world):
+        if hasattr(world, "materialize") and id(world) not in self.futures:
+            self.futures[id(world)] = self.pool.submit(world.materialize)
 
     def create(self, world):
+        if hasattr(world, "materialize"):
+            self.prepare(world)
+            world = self.futures.pop(id(world)).result()
         return self.coral.substrate_for_world(world, self.path)
 
     def batch(self, handles):
@@ -81,10 +94,12 @@ class WorldServer:
     """Admits requests by memory budget and steps the resident worlds as one batch."""
 
     def __init__(self, backend, budget_bytes: int, chunk_steps: int = 4, clock=time.perf_counter,
-                 sleep=time.sleep):
+                 sleep=time.sleep, max_worlds: int = 0, prefetch: int = 8):
         self.backend = backend
         self.budget = int(budget_bytes)
         self.chunk = max(1, int(chunk_steps))
+        self.max_worlds = int(max_worlds)      # batch slots (0 = bounded by the budget only)
+        self.prefetch = int(prefetch)          # queued requests whose worlds are built ahead
         self.clock = clock
         self.sleep = sleep
 
@@ -107,6 +122,9 @@ class WorldServer:
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.pop(0))
+            if hasattr(self.backend, "prepare"):
+                for r in waiting[:self.prefetch]:
+                    self.backend.prepare(r.world)
             # admission: arrival order, while the budget allows (a request that can never fit
             # on its own is rejected rather than blocking the queue)
             while waiting:
@@ -116,7 +134,7 @@ class WorldServer:
                     waiting.pop(0)
                     completed.append(Completed(r.rid, r.arrival, -1.0, -1.0, 0, r.world.n_cells, {}))
                     continue
-                if used + need > self.budget:
+                if used + need > self.budget or (self.max_worlds and len(active) >= self.max_worlds):
                     break
                 waiting.pop(0)
                 active[r.rid] = [r, self.backend.create(r.world), r.steps, self.clock() - t0, need]
@@ -178,7 +196,7 @@ class WorldServer:
             "mean_resident_worlds": float(np.mean([k for _, k in step_lat])) if step_lat else 0.0,
             "p50_queue_s": float(np.percentile([c.admitted - c.arrival for c in served], 50)) if served else 0.0,
             "p99_queue_s": float(np.percentile([c.admitted - c.arrival for c in served], 99)) if served else 0.0,
-            "peak_resident_bytes": peak_used, "budget_bytes": self.budget,
+            "peak_resident_bytes": peak_used, "budget_bytes": self.budget, "max_worlds": self.max_worlds,
         }
         return completed, report
 

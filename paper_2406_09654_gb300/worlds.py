@@ -98,6 +98,38 @@ def _torus_voronoi(width, height, n, rng):
     return G
 
 
+def _torus_voronoi_tree(width, height, n, rng):
+    """The same layout as _torus_voronoi (same seed draw, integer torus distance^2, ties to the
+    lower seed index), found with a periodic k-d tree: the two nearest seeds of each cell, and
+    a scan of every seed for the few cells where those two are at the same distance."""
+    from scipy.spatial import cKDTree
+    flat = rng.choice(width * height, size=n, replace=False)
+    sx, sy = flat % width, flat // width
+    G = np.zeros(width * height, np.int32)
+    if n == 1:
+        return G.reshape(height, width)
+    tree = cKDTree(np.stack([sx, sy], 1).astype(np.float64), boxsize=[width, height])
+    chunk = 1 << 20
+    for c0 in range(0, width * height, chunk):
+        c = np.arange(c0, min(width * height, c0 + chunk))
+        x, y = c % width, c // width
+        _, idx = tree.query(np.stack([x, y], 1).astype(np.float64), k=2, workers=-1)
+        dx = np.abs(x[:, None] - sx[idx])
+        dx = np.minimum(dx, width - dx)
+        dy = np.abs(y[:, None] - sy[idx])
+        dy = np.minimum(dy, height - dy)
+        d2 = dx * dx + dy * dy
+        g = idx[:, 0].copy()
+        for j in np.nonzero(d2[:, 1] == d2[:, 0])[0]:
+            ex = np.abs(x[j] - sx)
+            ex = np.minimum(ex, width - ex)
+            ey = np.abs(y[j] - sy)
+            ey = np.minimum(ey, height - ey)
+            g[j] = np.argmin(ex * ex + ey * ey)
+        G[c] = g
+    return G.reshape(height, width)
+
+
 def zipf_counts(total: int, n: int, s: float) -> np.ndarray:
     """Cell counts n_k proportional to k^-s (k = 1..n), rounded by largest remainder so that
     they sum to ``total``; remainder ties go to the lower rank."""
@@ -230,22 +262,12 @@ def make_world(preset: str | None = None, seed: int = 0, **overrides) -> World:
                  steps=int(cfg.get("steps", 1)), name=preset or "custom")
 
 
-def _block_voronoi(width, height, n, rng, block=8):
-    """Voronoi blobs computed on 8x8-cell blocks (seeds at block centres, torus distance in
-    blocks, ties to the lower seed), then expanded to cells: the layout of large worlds."""
-    bw, bh = -(-width // block), -(-height // block)
-    if n > bw * bh:
-        return _torus_voronoi(width, height, n, rng)
-    Gb = _torus_voronoi(bw, bh, n, rng)
-    return np.repeat(np.repeat(Gb, block, axis=0), block, axis=1)[:height, :width].astype(np.int32)
-
-
 def make_batch_worlds(n_worlds: int = 256, side_min: int = 128, side_max: int = 2048,
                       genomes=(16, 256), hidden: int = 32, seed: int = 0):
     """Independent square worlds for batched stepping: side log-uniform in [side_min, side_max],
     genome count uniform in the given range, CPPN nets 54->hidden->10, no radiation. Channels
-    are drawn in float32 (same distributions as make_world); genomes sit in Voronoi blobs
-    computed on 8x8-cell blocks."""
+    are drawn in float32 (same distributions as make_world); genomes sit in per-cell Voronoi
+    blobs."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, n_worlds, side_min, side_max, 4]))
     sides = np.rint(np.exp(rng.uniform(np.log(side_min), np.log(side_max), n_worlds))).astype(int)
     counts = rng.integers(genomes[0], genomes[1] + 1, n_worlds)
@@ -254,27 +276,47 @@ def make_batch_worlds(n_worlds: int = 256, side_min: int = 128, side_max: int = 
 
 
 def make_square_world(side: int, n_genomes: int, hidden: int = 32, seed: int = 0, name: str = "") -> World:
-    """One side x side world with n_genomes CPPN genomes in block-Voronoi blobs, no radiation;
-    channels drawn in float32 with make_world's distributions."""
+    """One side x side world with n_genomes CPPN genomes in Voronoi blobs (per cell, as
+    make_world), no radiation; channels drawn in float32 with make_world's distributions."""
     s, n = int(side), int(n_genomes)
     r = np.random.default_rng(np.random.SeedSequence([seed, s, n, hidden, 6]))
     E = r.random((s, s), dtype=np.float32)
     I = (0.5 * r.random((s, s), dtype=np.float32)).astype(np.float32)
     C = (0.1 * r.standard_normal((4, s, s), dtype=np.float32)).astype(np.float32)
-    G = _block_voronoi(s, s, min(n, s * s), r)
+    G = _torus_voronoi_tree(s, s, min(n, s * s), r)
     genes = r.normal(0.0, 1.0, (n, N_GENES)).astype(np.float32)
     phys = dict(DEFAULT_PHYSICS, radiation_every=0, p_mut=0.0, p_merge=0.0)
     return World(s, s, E, I, C, G, np.zeros((s, s), np.uint8), n, hidden, n, genes=genes,
                  physics=phys, seed=seed, steps=1, name=name or f"square{s}")
 
 
-def request_world_factory(side_range=(128, 4096), genomes_range=(8, 1024), hidden: int = 32):
+class LazySquareWorld:
+    """A serving request's world, described by its size up front (for admission) and built by
+    make_square_world on first use (materialize), so that a long request list holds no state."""
+
+    def __init__(self, side: int, n_genomes: int, hidden: int, seed: int, name: str):
+        self.width = self.height = int(side)
+        self.n_genomes = self.capacity = int(n_genomes)
+        self.hidden, self.seed, self.name = int(hidden), int(seed), name
+
+    @property
+    def n_cells(self) -> int:
+        return self.width * self.height
+
+    def materialize(self) -> World:
+        return make_square_world(self.width, self.n_genomes, self.hidden, seed=self.seed, name=self.name)
+
+
+def request_world_factory(side_range=(128, 4096), genomes_range=(8, 1024), hidden: int = 32, lazy: bool = False):
     """make_world(rng, k) for serving requests: side log-uniform in side_range, genome count
-    uniform in genomes_range (capped by the cell count)."""
+    uniform in genomes_range (capped by the cell count); lazy: a LazySquareWorld."""
     def make(rng, k):
         side = int(np.rint(np.exp(rng.uniform(np.log(side_range[0]), np.log(side_range[1])))))
-        n = int(rng.integers(genomes_range[0], genomes_range[1] + 1))
-        return make_square_world(side, min(n, side * side), hidden, seed=int(rng.integers(1 << 30)), name=f"req{k}")
+        n = min(int(rng.integers(genomes_range[0], genomes_range[1] + 1)), side * side)
+        seed = int(rng.integers(1 << 30))
+        if lazy:
+            return LazySquareWorld(side, n, hidden, seed, f"req{k}")
+        return make_square_world(side, n, hidden, seed=seed, name=f"req{k}")
     return make
 
 

@@ -102,3 +102,34 @@ def test_poisson_requests_are_sorted_and_seeded():
     assert [r.arrival for r in a] == [r.arrival for r in b]
     assert all(x.arrival < y.arrival for x, y in zip(a, b[1:]))
     assert all(16 <= r.world.width <= 64 and 10 <= r.steps <= 20 for r in a)
+
+
+def test_batch_slots_bound_resident_worlds_and_queue_requests():
+    clock = FakeClock()
+    be = FakeBackend(clock)
+    reqs = [serving.Request(0.001 * k, k, small(k), 5) for k in range(12)]
+    srv = serving.WorldServer(be, budget_bytes=1 << 40, chunk_steps=2, clock=clock, sleep=clock.sleep, max_worlds=4)
+    done, rep = srv.run(reqs)
+    assert rep["served"] == 12 and all(len(b) <= 4 for b in be.batches)
+    assert rep["p99_queue_s"] > 0 and rep["max_worlds"] == 4
+    assert all(c.result["steps"] == 5 for c in done)
+    assert rep["p50_step_wall_ms"] >= 0 and rep["p99_request_ms_per_step"] >= rep["p50_request_ms_per_step"]
+
+
+def test_lazy_request_worlds_match_eager_ones():
+    f_lazy = worlds.request_world_factory((16, 64), (2, 9), lazy=True)
+    f_eager = worlds.request_world_factory((16, 64), (2, 9))
+    a = serving.poisson_requests(5, 100.0, f_lazy, (3, 9), seed=2)
+    b = serving.poisson_requests(5, 100.0, f_eager, (3, 9), seed=2)
+    for ra, rb in zip(a, b):
+        assert ra.world.n_cells == rb.world.n_cells and ra.world.capacity == rb.world.capacity
+        w = ra.world.materialize()
+        for k in ("E", "I", "C", "G", "R"):
+            assert np.array_equal(getattr(w, k), getattr(rb.world, k))
+
+
+def test_tree_voronoi_equals_plain_voronoi():
+    for W, H, n, seed in [(37, 29, 5, 1), (64, 64, 60, 2), (300, 200, 256, 3), (7, 5, 35, 4), (10, 10, 1, 5)]:
+        a = worlds._torus_voronoi(W, H, n, np.random.default_rng(seed))
+        b = worlds._torus_voronoi_tree(W, H, n, np.random.default_rng(seed))
+        assert np.array_equal(a, b)
