@@ -6,8 +6,9 @@
 // builds the 128 x 64 BF16 input tile (the rotation-ordered 3x3 neighbourhood of every cell, K
 // index 6*rank + channel, a constant 1 at K = 54 that carries the layer-1 bias) and runs the
 // genome nets on the tensor cores with FP32 accumulation in TMEM: one 128 x H x 64 MMA for
-// layer 1, tanh in the epilogue (the hidden tile overwrites the consumed input tile, layer 2
-// reuses the TMEM columns), one 128 x 16 x H MMA for layer 2. A tile with several genomes runs
+// layer 1 (both operands in shared memory), tanh in the epilogue with the BF16 hidden tile
+// written back into the consumed TMEM columns, one 128 x 16 x H MMA for layer 2 that reads
+// its A operand from TMEM. A tile with several genomes runs
 // one round per genome (the rows of other genomes are computed and discarded); a cell's
 // actuator epilogue (communication, invest/liquidate, exploration, flow quotient) runs in
 // registers in the round that computes its outputs.
@@ -28,7 +29,10 @@ constexpr int kCtasPerSm = 5;                             // 5 x 64 of the 512 T
 constexpr int kTileW = 32, kTileH = kThreads / kTileW;   // thread q: cell (q % kTileW, q / kTileW)
 constexpr int kHaloW = kTileW + 2, kHaloH = kTileH + 2;
 constexpr int kHaloCells = kHaloW * kHaloH;
-constexpr uint32_t kTmemCols = 64;                        // layer 1, then layer 2 in cols 0..15
+// TMEM columns of a CTA: layer 1's FP32 accumulators in 0..H-1; the BF16 hidden tile is
+// written over its first H/2 columns; layer 2's accumulators in kD2Col..kD2Col+15
+constexpr uint32_t kTmemCols = 64;
+constexpr uint32_t kD2Col = 32;
 constexpr long long kWaitCycles = 4000000000LL;           // about 2 s of SM clock
 // Work split: each CTA first takes a contiguous run of about half its share of the tiles
 // (neighbouring tiles share halo rows in L2 and usually a genome); the remaining tiles form a
@@ -319,8 +323,8 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     }
     // One tensor-core round per genome present in the tile: first the genome whose blob is
     // already staged, if the tile has cells of it, then the first pending row's genome.
-    // The input rows of pending cells survive a round (only finished rows are overwritten by
-    // their hidden values), so the input tile is built once per tile. Each round publishes the
+    // The input tile in shared memory survives the rounds (the hidden tile lives in TMEM), so
+    // it is built once per tile. Each round publishes the
     // rows still pending after it in the other ballot buffer before its first barrier, so the
     // tile ends without a further barrier; the MMAs' completion is awaited by every thread on
     // the mbarrier, not through a CTA barrier.
@@ -410,21 +414,22 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
           finish(act, v);
         }
       } else {
-        // hidden layer: tanh, BF16, written over this row of the (consumed) input tile
+        // hidden layer: tanh, packed to BF16 and written over the consumed layer-1 columns of
+        // this thread's TMEM lane (BF16 column pair c holds hidden units 2c, 2c + 1): the
+        // layer-2 A operand. Chunk c16's 8 packed columns lie inside the 16 columns it was
+        // loaded from or an earlier chunk's. The store is warp-wide; rows of other genomes
+        // store values that only their discarded layer-2 outputs use.
 #pragma unroll
         for (int c16 = 0; c16 < N1 / 16; ++c16) {
           float v[16];
           tc::tmem_ld16(t_lane + c16 * 16, v);
           tc::tmem_wait_ld();
-          if (mine) {
-            uint32_t pk[8];
+          uint32_t pk[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) pk[i] = tc::pack_bf16x2(tc::tanh_approx(v[2 * i]), tc::tanh_approx(v[2 * i + 1]));
-            tc::sts128(row_s + (((2 * c16) ^ (tid & 7)) << 4), pk[0], pk[1], pk[2], pk[3]);
-            tc::sts128(row_s + (((2 * c16 + 1) ^ (tid & 7)) << 4), pk[4], pk[5], pk[6], pk[7]);
-          }
+          for (int i = 0; i < 8; ++i) pk[i] = tc::pack_bf16x2(tc::tanh_approx(v[2 * i]), tc::tanh_approx(v[2 * i + 1]));
+          tc::tmem_st8(t_lane + c16 * 8, pk);
         }
-        tc::fence_proxy_async();
+        tc::tmem_wait_st();
         tc::tc_fence_before();
         if (__syncthreads_or(bad)) {
           timed_out = true;
@@ -432,16 +437,16 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
         }
         if (tid == 0) {
           tc::tc_fence_after();
-          const uint64_t ad = tc::sdesc_sw128(a_s), bd = tc::sdesc_sw128(w_s + bf16_w2_off(H));
+          const uint64_t bd = tc::sdesc_sw128(w_s + bf16_w2_off(H));
 #pragma unroll
-          for (int k = 0; k < N1 / 16; ++k) tc::mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc2, k > 0);
+          for (int k = 0; k < N1 / 16; ++k) tc::mma_bf16_ts(tmem + kD2Col, tmem + 8 * k, bd + 2 * k, idesc2, k > 0);
           tc::mma_commit(mbar);
         }
         if (!tc::mbar_wait(mbar, phase, kWaitCycles)) bad = true;
         phase ^= 1;
         tc::tc_fence_after();
         float v[16];
-        tc::tmem_ld16(t_lane, v);
+        tc::tmem_ld16(t_lane + kD2Col, v);
         tc::tmem_wait_ld();
         if (mine) {
           const float* b2 = reinterpret_cast<const float*>(base + kOffW + bf16_b2_off(H));
