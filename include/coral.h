@@ -263,7 +263,7 @@ int coral_batch_step(coral_batch* b, int32_t n_steps);
 int coral_batch_step_timed(coral_batch* b, int32_t n_steps, float* step_ms);
 /*
  * Autotuner: times trial_steps steps (after one warm-up) for each candidate launch shape —
- * pass-1 CTAs per SM in {2, 3, 4, 5} x pass-2 CTAs per SM in {1, 2, 3}, each times 32 as
+ * pass-1 CTAs per SM in {3, 4, 5, 6} x pass-2 CTAs per SM in {1, 2, 3}, each times 32 as
  * above — keeps the fastest and
  * restores every world's state, step index and stats ring afterwards (also after an error,
  * which leaves the launch shape the batch had before the call; a failed save or restore copy

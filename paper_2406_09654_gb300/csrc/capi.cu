@@ -772,7 +772,7 @@ struct coral_batch {
   long long* d_steps = nullptr;
   CUtensorMap* d_tmaps = nullptr;  // [2][n]
   int* d_tma_ok = nullptr;         // [n]
-  int cps1 = 5, cps2 = 3;        // CTAs per SM of pass 1 / pass 2
+  int cps1 = 6, cps2 = 3;        // CTAs per SM of pass 1 / pass 2
   int grid1 = 0, grid2 = 0;
   int max_grid = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -976,7 +976,7 @@ extern "C" int coral_batch_create(coral_substrate* const* worlds, int32_t n, cor
     }
     if (rc) break;
     b->sms = worlds[0]->sms;
-    b->max_grid = std::max(5 * b->sms * kOversubscribe, n) + 8;
+    b->max_grid = std::max(6 * b->sms * kOversubscribe, n) + 8;
     cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev, cudaEventDisableTiming);
     const size_t bytes = sizeof(StepArgs) * 2 * (size_t)n + 256 + sizeof(int) * (4 * (size_t)b->max_grid + 6 * (size_t)n) +
@@ -1094,7 +1094,7 @@ extern "C" int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* ch
                    std::string("saving the states for tuning: ") + cudaGetErrorString(e));
     }
   }
-  const int c1s[4] = {2, 3, 4, 5}, c2s[3] = {1, 2, 3};
+  const int c1s[4] = {3, 4, 5, 6}, c2s[3] = {1, 2, 3};
   float best = 1e30f;
   int b1 = cps1_0, b2 = cps2_0, rc = CORAL_OK;
   std::vector<float> ms(trial_steps + 1);

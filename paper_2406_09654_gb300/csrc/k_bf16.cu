@@ -25,7 +25,7 @@ namespace coral {
 namespace {
 
 constexpr int kThreads = 128;
-constexpr int kCtasPerSm = 5;                             // 5 x 64 of the 512 TMEM columns
+constexpr int kCtasPerSm = 6;                             // 6 x 64 of the 512 TMEM columns, 80 registers
 constexpr int kTileW = 32, kTileH = kThreads / kTileW;   // thread q: cell (q % kTileW, q / kTileW)
 constexpr int kHaloW = kTileW + 2, kHaloH = kTileH + 2;
 constexpr int kHaloCells = kHaloW * kHaloH;
@@ -61,6 +61,23 @@ constexpr int kOffRec = kOffStage + kStageBytes;          // 204 x 16 B BF16 cel
 constexpr int kOffG = kOffRec + kHaloCells * 16;          // int32 [128]
 constexpr int kOffMisc = kOffG + 512;                     // mbarrier, TMEM slot, flags
 constexpr int kSmemBytes = kOffMisc + 128 + 1024;         // + alignment slack
+
+// C' * 2^26 as an integer from the float's bits: C' lies in (0.26, 0.74), so its exponent is
+// 2^-2 or 2^-1 and the value is the 24-bit significand shifted left by 1 or 2 (exact; integer
+// operations instead of a float-to-int conversion on the special-function pipe).
+__device__ __forceinline__ int cfix(float c) {
+  const uint32_t b = __float_as_uint(c);
+  return (int)(((b & 0x7FFFFFu) | 0x800000u) << ((b >> 23) - 124u));
+}
+
+// Exact float -> double by moving the bits (rebias the exponent, shift the significand), for
+// normal floats; returns false in `special` for zero, subnormal, infinite or NaN inputs, which
+// the caller converts on the FP64 pipe instead.
+__device__ __forceinline__ double f2d_bits(float f, bool& special) {
+  const uint32_t b = __float_as_uint(f), a = b & 0x7FFFFFFFu;
+  special |= (a - 0x00800000u) >= 0x7F000000u;
+  return __hiloint2double((int)(((a >> 3) + 0x38000000u) | (b & 0x80000000u)), (int)(b << 29));
+}
 
 // v in [-1, n + tile) folded onto [0, n): one conditional step when the torus side is at least
 // the halo's (small), else a full modulo.
@@ -276,7 +293,15 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       const float* sI = stage + kStageCh;
       Ec = stage[sc];
       Ic = sI[sc];
-      Sf = (float)((double)sI[sc - kStageW] + (double)sI[sc + 1] + (double)sI[sc + kStageW] + (double)sI[sc - 1]);
+      // the four neighbours' I in double precision: exact bit moves unless a value is zero,
+      // subnormal or not finite somewhere in the warp (then the FP64 conversions)
+      const float iN = sI[sc - kStageW], iE = sI[sc + 1], iS = sI[sc + kStageW], iW = sI[sc - 1];
+      bool sp = false;
+      const double dN = f2d_bits(iN, sp), dE = f2d_bits(iE, sp), dS = f2d_bits(iS, sp), dW = f2d_bits(iW, sp);
+      if (__any_sync(0xffffffffu, sp))
+        Sf = (float)((double)iN + (double)iE + (double)iS + (double)iW);
+      else
+        Sf = (float)(dN + dE + dS + dW);
     }
     bool done = g < 0;
     rb ^= 1;                                          // the last round's buffer is free again
@@ -314,7 +339,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       actuator_epilogue<true>(a, act, zo, Ec, Ic, Sf, r, o);
       store_pass1(a, j, o);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) cacc[k] += __float2int_rn(o.C[k] * kCFix);
+      for (int k = 0; k < 4; ++k) cacc[k] += cfix(o.C[k]);
       accX += o.xdir != kNoExplore ? 1 : 0;
     };
     if (valid && g < 0) {                             // empty cell: all actuators at zero

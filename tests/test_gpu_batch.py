@@ -62,7 +62,7 @@ def test_batch_tuner_restores_state_and_mixes_with_single_steps():
     try:
         with coral.Batch(subs) as b:
             choice = b.tune(trial_steps=2)
-            assert choice["pass1_ctas_per_sm"] in (2, 3, 4, 5) and choice["pass2_ctas_per_sm"] in (1, 2, 3)
+            assert choice["pass1_ctas_per_sm"] in (3, 4, 5, 6) and choice["pass2_ctas_per_sm"] in (1, 2, 3)
             subs[0].step(1)                          # one world steps alone in between
             b.step(2)
         for w, s, extra in zip(ws, subs, [1, 0, 0, 0, 0]):
