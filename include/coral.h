@@ -83,9 +83,6 @@ typedef struct coral_params {
   float sigma_mut;         /* std of the Gaussian added to every gene by a mutation (0.05) */
   uint32_t world;          /* Philox counter word 3 (distinguishes independent worlds) */
   uint64_t seed;           /* Philox key */
-  int32_t fma_cutoff;      /* BF16 path: a genome with fewer cells than this in a 128-cell
-                              tile runs on the warp FMA path instead of the tensor cores */
-  int32_t max_mma_genomes; /* BF16 path: at most this many genomes per tile use tcgen05 */
 } coral_params;
 
 /* Per-step record kept in a device ring (read with coral_read_stats). */

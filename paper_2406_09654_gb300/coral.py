@@ -37,7 +37,6 @@ class Params(ctypes.Structure):
         ("radiation_every", ctypes.c_int32), ("p_mut", ctypes.c_double),
         ("p_merge", ctypes.c_double), ("sigma_mut", ctypes.c_float),
         ("world", ctypes.c_uint32), ("seed", ctypes.c_uint64),
-        ("fma_cutoff", ctypes.c_int32), ("max_mma_genomes", ctypes.c_int32),
     ]
 
 

@@ -132,8 +132,6 @@ StepArgs step_args(const coral_substrate* s) {
   a.blob_bytes = s->g.blob_bytes;
   a.part1 = s->part1;
   a.part2 = s->part2;
-  a.fma_cutoff = s->p.fma_cutoff;
-  a.max_mma_genomes = s->p.max_mma_genomes;
   a.status = s->status;
   a.day_period = s->p.day_period;
   a.capacity = s->cap;
@@ -182,8 +180,6 @@ int coral_params_default(coral_params* p) {
   p->sigma_mut = 0.05f;
   p->world = 0;
   p->seed = 0;
-  p->fma_cutoff = 8;
-  p->max_mma_genomes = 2;
   return CORAL_OK;
 }
 
@@ -202,8 +198,6 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
   if (p->radiation_every < 0) return fail(nullptr, CORAL_E_INVALID, "radiation_every must be >= 0");
   if (!(p->p_mut >= 0.0 && p->p_mut <= 1.0) || !(p->p_merge >= 0.0 && p->p_merge <= 1.0))
     return fail(nullptr, CORAL_E_INVALID, "p_mut and p_merge must be in [0, 1]");
-  if (p->path == CORAL_NET_BF16_GROUPED && (p->max_mma_genomes < 1 || p->max_mma_genomes > 4))
-    return fail(nullptr, CORAL_E_INVALID, "max_mma_genomes must be in [1, 4]");
   coral_substrate* s = nullptr;
   try {
     s = new coral_substrate();

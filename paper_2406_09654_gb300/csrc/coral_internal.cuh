@@ -98,8 +98,6 @@ struct __align__(8) StepArgs {
   int blob_bytes;
   Partial* part1;   // written by pass 1 (C sums, explore count)
   Partial* part2;   // written by pass 2 (E, I sums, takeover count)
-  int fma_cutoff;
-  int max_mma_genomes;
   int* status;
   int day_period;
   int capacity;     // genome slots: a GenomeIndex outside [0, capacity) acts as "no genome"

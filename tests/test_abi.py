@@ -44,7 +44,7 @@ def test_defaults_and_net_floats(lib):
     assert (p.hidden, p.path, p.day_period, p.rotation) == (0, 0, 200, 1)
     assert p.k_inv == pytest.approx(0.1) and p.k_exp == pytest.approx(0.5)
     assert p.k_flow == pytest.approx(0.2) and p.sigma_mut == pytest.approx(0.05)
-    assert p.fma_cutoff == 8 and p.max_mma_genomes == 2 and p.seed == 0
+    assert p.seed == 0 and p.p_mut == 0.0 and p.p_merge == 0.0
     assert coral.net_floats(0) == 550 and coral.net_floats(64) == 64 * 54 + 64 + 640 + 10
 
 
