@@ -297,6 +297,62 @@ int coral_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out,
  */
 int coral_measure_sfu_rate(void* cuda_stream, double* evals_per_s);
 
+/*
+ * Row slabs: one world split into horizontal slabs of rows, one substrate per slab (a logical
+ * rank; on several GPUs one rank per device). Section "System Design" updates every cell of the
+ * substrate synchronously from its neighbourhood, so a slab with copies of its neighbours' rows
+ * steps its own rows exactly as the whole world would. A slab substrate is width x (own rows +
+ * 6): 3 ghost rows above and below the own rows, refreshed from the neighbouring slabs' own rows
+ * before every step (coral_copy_rows). A step's new state depends on the old state within two
+ * rows, and radiation's merge partner is one row away, whose post-step state the third ghost
+ * row gives exactly. The library keeps no list of slabs: the caller exchanges the rows and runs
+ * the radiation protocol (scan every slab, combine, apply every slab), so that the slabs may
+ * live in different processes. The results (state, genome table, radiation decisions) are
+ * bit-identical to stepping the whole world in one substrate.
+ *
+ * coral_slab_set: rows [row_lo, row_hi) of s are its own rows (1 <= row_lo < row_hi <=
+ * height - 1), the global id of cell (row_lo, 0) is global_cell0 (the Philox counter and the
+ * order of radiation hits use global ids; ids stay below 2^32). From then on coral_step runs no
+ * radiation on s, and coral_slab_totals / the radiation calls act on the own rows only.
+ */
+int coral_slab_set(coral_substrate* s, int32_t row_lo, int32_t row_hi, int64_t global_cell0);
+
+/*
+ * Copies rows [src_row, src_row + n_rows) of every plane (E, I, C0..C3, G, R) of src's current
+ * state into rows [dst_row, dst_row + n_rows) of dst's current state (device to device, same
+ * width and device; src == dst allowed for disjoint ranges: a single slab's ghost rows). The
+ * copy is ordered after the work enqueued on src's stream, and src's later work after the copy.
+ * Returns after enqueueing. Errors: E_INVALID (widths, devices, row ranges), E_CUDA.
+ */
+int coral_copy_rows(coral_substrate* dst, int32_t dst_row, coral_substrate* src, int32_t src_row, int32_t n_rows);
+
+/* FP64 totals (E, I, C0..C3) over the own rows of a slab (all rows otherwise), fixed summation
+ * order: out[6] host. Synchronises. (A slab's stats ring counts its ghost rows too.) */
+int coral_slab_totals(coral_substrate* s, double* out);
+
+/*
+ * Radiation of a slab, first half (Fig. 1 C; readings R10-R12), for the step that just ran
+ * (step index coral_get_step - 1): which genome slots own a cell among the own rows, and the own
+ * rows' hits in increasing global cell order. live: host uint8 [capacity] (1 = the slot owns an
+ * own cell); hits: host int32 [max_hits][5] = (global cell id, parent slot, merge partner slot
+ * or -1, flags: 1 mutation | 2 merge, crossover bits); counts: host int32 [4] = (hits, mutation
+ * hits, merge hits, hits listed = min(hits, capacity, max_hits)). Synchronises.
+ * Errors: E_STATE (not a slab, no CPPN genomes, no step yet), E_INVALID.
+ */
+int coral_slab_radiation_scan(coral_substrate* s, uint8_t* live, int32_t* hits, int32_t max_hits, int32_t* counts);
+
+/*
+ * Radiation of a slab, second half: live_all = the OR of every slab's live flags; hits_all =
+ * every slab's listed hits concatenated in slab order (the global cell order), n_listed rows;
+ * counts_all = the sums over the slabs of counts[0..2]. Assigns the lowest free slots to the hits
+ * in order (hits beyond the free slots are skipped and counted), writes every child genome into
+ * this slab's genome table (each slab holds the whole table), sets G of the own cells among the
+ * hits, regenerates the new slots' nets and writes the event counts into the stats record of the
+ * step. Every slab must be given the same arguments. Synchronises. Errors: E_STATE, E_INVALID.
+ */
+int coral_slab_radiation_apply(coral_substrate* s, const uint8_t* live_all, const int32_t* hits_all,
+                               int32_t n_listed, const int32_t* counts_all);
+
 /* Waits for the stream and returns the first latched device-side error, if any. */
 int coral_sync(coral_substrate* s);
 

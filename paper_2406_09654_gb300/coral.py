@@ -90,6 +90,11 @@ SIGNATURES = {
     "coral_bucket_noalloc_last_error": (ctypes.c_char_p, []),
     "coral_philox4x32_10": (ctypes.c_int, [_VP, _VP, _VP, _I32]),
     "coral_measure_sfu_rate": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double)]),
+    "coral_slab_set": (ctypes.c_int, [_VP, _I32, _I32, _I64]),
+    "coral_copy_rows": (ctypes.c_int, [_VP, _I32, _VP, _I32, _I32]),
+    "coral_slab_totals": (ctypes.c_int, [_VP, _VP]),
+    "coral_slab_radiation_scan": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP]),
+    "coral_slab_radiation_apply": (ctypes.c_int, [_VP, _VP, _VP, _I32, _VP]),
 }
 
 _lib = None
@@ -328,6 +333,34 @@ class Substrate:
         out = np.empty((len(sl), len(sl)), np.float32)
         _check(lib().coral_genome_distances(self.h, sl.ctypes.data, len(sl), out.ctypes.data), self.h)
         return out
+
+    # -- row slabs (see coral_slab_set in include/coral.h)
+    def slab_set(self, row_lo, row_hi, global_cell0):
+        _check(lib().coral_slab_set(self.h, int(row_lo), int(row_hi), int(global_cell0)), self.h)
+
+    def copy_rows_from(self, dst_row, src, src_row, n_rows):
+        _check(lib().coral_copy_rows(self.h, int(dst_row), src.h, int(src_row), int(n_rows)), self.h)
+
+    def slab_totals(self):
+        out = np.empty(6, np.float64)
+        _check(lib().coral_slab_totals(self.h, out.ctypes.data), self.h)
+        return out
+
+    def slab_radiation_scan(self):
+        """(live uint8 [capacity], hits int32 [listed][5], counts int32 [4])."""
+        live = np.empty(self.capacity, np.uint8)
+        hits = np.empty((self.capacity, 5), np.int32)
+        counts = np.empty(4, np.int32)
+        _check(lib().coral_slab_radiation_scan(self.h, live.ctypes.data, hits.ctypes.data, self.capacity,
+                                               counts.ctypes.data), self.h)
+        return live, hits[:counts[3]].copy(), counts
+
+    def slab_radiation_apply(self, live_all, hits_all, counts_all):
+        live = np.ascontiguousarray(live_all, np.uint8)
+        hits = np.ascontiguousarray(hits_all, np.int32).reshape(-1, 5)
+        counts = np.ascontiguousarray(counts_all, np.int32)
+        _check(lib().coral_slab_radiation_apply(self.h, live.ctypes.data, hits.ctypes.data if len(hits) else None,
+                                                len(hits), counts.ctypes.data), self.h)
 
     def read_weights(self, slot):
         nf = lib().coral_net_floats(self.params.hidden)

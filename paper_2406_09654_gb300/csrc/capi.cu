@@ -61,6 +61,12 @@ struct coral_substrate {
   long long t = 0;
   int grid1 = 0, grid2 = 0;
   JobPipe jobs;
+  // row slab of a larger world (coral_slab_set): own rows [row_lo, row_hi), global id of the
+  // first own cell; radiation then runs through coral_slab_radiation_scan / _apply
+  bool slab = false;
+  int row_lo = 0, row_hi = 0;
+  long long gid0 = 0;
+  double* totals_buf = nullptr;  // coral_slab_totals: 6 totals + per-block partials
   std::string err;
 };
 
@@ -377,6 +383,37 @@ int coral_cppn_generate_weights(coral_substrate* s, const int32_t* slots, int32_
 
 namespace {
 
+// Radiation arguments of the step that just ended (index t), over the substrate's own cells.
+RadiationArgs radiation_args(coral_substrate* s, long long t) {
+  RadiationArgs r = {};
+  r.W = s->W;
+  r.H = s->H;
+  r.N = s->N;
+  r.G = s->st[s->cur].G;
+  r.j0 = s->slab ? (long long)s->row_lo * s->W : 0;
+  r.n_own = s->slab ? (long long)(s->row_hi - s->row_lo) * s->W : s->N;
+  r.gid0 = s->slab ? s->gid0 : 0;
+  r.g = s->g;
+  r.thr_mut = hit_threshold(s->p.p_mut);
+  r.thr_merge = hit_threshold(s->p.p_merge);
+  r.sigma = s->p.sigma_mut;
+  r.world = s->p.world;
+  r.seed = s->p.seed;
+  r.step = (uint32_t)t;
+  r.count = s->count;
+  r.hitmask = s->hitmask;
+  r.blockcnt = s->blockcnt;
+  r.blockoff = s->blockoff;
+  r.hits = s->hits;
+  r.hitbits = s->hitbits;
+  r.max_hits = s->cap;
+  r.freelist = s->freelist;
+  r.newslots = s->newslots;
+  r.counters = s->counters;
+  r.rec = s->ring + (t % kRing);
+  return r;
+}
+
 // Enqueues one step; ev (4 events or NULL) is recorded before pass 1, after pass 1, after
 // pass 2 and after the totals / radiation.
 int enqueue_step(coral_substrate* s, cudaEvent_t* ev) {
@@ -391,32 +428,8 @@ int enqueue_step(coral_substrate* s, cudaEvent_t* ev) {
   if (ev) CK(s, cudaEventRecord(ev[2], s->stream));
   CK(s, launch_stats(a, s->grid1, s->grid2, s->t, s->ring, s->stream));
   s->cur ^= 1;
-  if (s->p.radiation_every > 0 && (s->t + 1) % s->p.radiation_every == 0) {
-    RadiationArgs r = {};
-    r.W = s->W;
-    r.H = s->H;
-    r.N = s->N;
-    r.G = s->st[s->cur].G;
-    r.g = s->g;
-    r.thr_mut = hit_threshold(s->p.p_mut);
-    r.thr_merge = hit_threshold(s->p.p_merge);
-    r.sigma = s->p.sigma_mut;
-    r.world = s->p.world;
-    r.seed = s->p.seed;
-    r.step = (uint32_t)s->t;
-    r.count = s->count;
-    r.hitmask = s->hitmask;
-    r.blockcnt = s->blockcnt;
-    r.blockoff = s->blockoff;
-    r.hits = s->hits;
-    r.hitbits = s->hitbits;
-    r.max_hits = s->cap;
-    r.freelist = s->freelist;
-    r.newslots = s->newslots;
-    r.counters = s->counters;
-    r.rec = s->ring + (s->t % kRing);
-    CK(s, launch_radiation(r, s->stream));
-  }
+  if (!s->slab && s->p.radiation_every > 0 && (s->t + 1) % s->p.radiation_every == 0)
+    CK(s, launch_radiation(radiation_args(s, s->t), s->stream));
   if (ev) CK(s, cudaEventRecord(ev[3], s->stream));
   ++s->t;
   return CORAL_OK;
@@ -735,6 +748,130 @@ int coral_measure_sfu_rate(void* cuda_stream, double* evals_per_s) {
   if (e != cudaSuccess) return fail(nullptr, CORAL_E_CUDA, std::string("sfu probe: ") + cudaGetErrorString(e));
   *evals_per_s = (double)blocks * 256.0 * 8.0 * iters / (ms * 1e-3);
   return CORAL_OK;
+}
+
+int coral_slab_set(coral_substrate* s, int32_t row_lo, int32_t row_hi, int64_t global_cell0) {
+  if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
+  if (row_lo < 1 || row_hi <= row_lo || row_hi > s->H - 1 || global_cell0 < 0)
+    return fail(s, CORAL_E_INVALID, "own rows must satisfy 1 <= row_lo < row_hi <= height - 1, global_cell0 >= 0");
+  if (global_cell0 + (long long)(row_hi - row_lo) * s->W > (1LL << 32))
+    return fail(s, CORAL_E_INVALID, "global cell ids must stay below 2^32");
+  s->slab = true;
+  s->row_lo = row_lo;
+  s->row_hi = row_hi;
+  s->gid0 = global_cell0;
+  return CORAL_OK;
+}
+
+int coral_copy_rows(coral_substrate* dst, int32_t dst_row, coral_substrate* src, int32_t src_row, int32_t n_rows) {
+  if (!dst || !src) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
+  if (dst->W != src->W) return fail(dst, CORAL_E_INVALID, "substrates of different widths");
+  if (dst->device != src->device) return fail(dst, CORAL_E_INVALID, "substrates on different devices");
+  if (n_rows < 0 || dst_row < 0 || src_row < 0 || dst_row + n_rows > dst->H || src_row + n_rows > src->H)
+    return fail(dst, CORAL_E_INVALID, "row range outside a substrate");
+  if (n_rows == 0) return CORAL_OK;
+  if (dst == src && dst_row < src_row + n_rows && src_row < dst_row + n_rows)
+    return fail(dst, CORAL_E_INVALID, "overlapping row ranges");
+  // order: the copies after src's enqueued work; src's later work after the copies
+  cudaEvent_t ev = nullptr;
+  CK(dst, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, src->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(dst->stream, ev, 0);
+  const Planes& d = dst->st[dst->cur];
+  const Planes& q = src->st[src->cur];
+  const size_t W = (size_t)dst->W, rows = (size_t)n_rows;
+  for (int p = 0; p < 6 && e == cudaSuccess; ++p)
+    e = cudaMemcpyAsync(d.E + (size_t)p * dst->N + dst_row * W, q.E + (size_t)p * src->N + src_row * W,
+                        sizeof(float) * rows * W, cudaMemcpyDeviceToDevice, dst->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d.G + dst_row * W, q.G + src_row * W, sizeof(int32_t) * rows * W, cudaMemcpyDeviceToDevice,
+                        dst->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d.R + dst_row * W, q.R + src_row * W, rows * W, cudaMemcpyDeviceToDevice, dst->stream);
+  if (e == cudaSuccess && src->stream != dst->stream) {
+    e = cudaEventRecord(ev, dst->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(src->stream, ev, 0);
+  }
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) return cuda_fail(dst, e, "copy rows");
+  return CORAL_OK;
+}
+
+int coral_slab_totals(coral_substrate* s, double* out) {
+  if (!s || !out) return fail(s, CORAL_E_INVALID, "NULL argument");
+  if (!s->totals_buf) CK(s, dalloc(s, &s->totals_buf, 6 + 6 * 256));
+  const long long j0 = s->slab ? (long long)s->row_lo * s->W : 0;
+  const long long n = s->slab ? (long long)(s->row_hi - s->row_lo) * s->W : s->N;
+  CK(s, launch_row_totals(s->st[s->cur].E, s->N, j0, n, s->totals_buf, s->stream));
+  CK(s, cudaMemcpyAsync(out, s->totals_buf, 6 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  return check_status(s);
+}
+
+int coral_slab_radiation_scan(coral_substrate* s, uint8_t* live, int32_t* hits, int32_t max_hits, int32_t* counts) {
+  if (!s || !live || !counts || (max_hits > 0 && !hits)) return fail(s, CORAL_E_INVALID, "NULL argument");
+  if (!s->slab) return fail(s, CORAL_E_STATE, "not a slab (coral_slab_set)");
+  if (!s->has_cppn) return fail(s, CORAL_E_STATE, "radiation needs CPPN genomes");
+  if (s->t < 1) return fail(s, CORAL_E_STATE, "no step has run yet");
+  CK(s, launch_radiation_scan(radiation_args(s, s->t - 1), s->stream));
+  int c[8];
+  CK(s, cudaMemcpyAsync(c, s->counters, sizeof(c), cudaMemcpyDeviceToHost, s->stream));
+  std::vector<int32_t> flags(s->cap);
+  CK(s, cudaMemcpyAsync(flags.data(), s->count, sizeof(int32_t) * s->cap, cudaMemcpyDeviceToHost, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));
+  const int listed = std::min(std::min(c[0], s->cap), std::max(max_hits, 0));
+  std::vector<int4> h(listed > 0 ? listed : 1);
+  std::vector<uint32_t> bits(listed > 0 ? listed : 1);
+  if (listed > 0) {
+    CK(s, cudaMemcpy(h.data(), s->hits, sizeof(int4) * listed, cudaMemcpyDeviceToHost));
+    CK(s, cudaMemcpy(bits.data(), s->hitbits, sizeof(uint32_t) * listed, cudaMemcpyDeviceToHost));
+  }
+  for (int i = 0; i < listed; ++i) {
+    int32_t* o = hits + 5 * (size_t)i;
+    o[0] = h[i].x;
+    o[1] = h[i].y;
+    o[2] = h[i].z;
+    o[3] = h[i].w;
+    o[4] = (int32_t)bits[i];
+  }
+  for (int k = 0; k < s->cap; ++k) live[k] = flags[k] ? 1 : 0;
+  counts[0] = c[0];
+  counts[1] = c[3];
+  counts[2] = c[4];
+  counts[3] = listed;
+  return check_status(s);
+}
+
+int coral_slab_radiation_apply(coral_substrate* s, const uint8_t* live_all, const int32_t* hits_all,
+                               int32_t n_listed, const int32_t* counts_all) {
+  if (!s || !live_all || !counts_all || (n_listed > 0 && !hits_all)) return fail(s, CORAL_E_INVALID, "NULL argument");
+  if (!s->slab) return fail(s, CORAL_E_STATE, "not a slab (coral_slab_set)");
+  if (s->t < 1) return fail(s, CORAL_E_STATE, "no step has run yet");
+  if (n_listed < 0 || counts_all[0] < n_listed || counts_all[0] < 0)
+    return fail(s, CORAL_E_INVALID, "hit counts inconsistent with the list");
+  const int up = std::min(n_listed, s->cap);
+  std::vector<int32_t> flags(s->cap);
+  for (int k = 0; k < s->cap; ++k) flags[k] = live_all[k] ? 1 : 0;
+  std::vector<int4> h(up > 0 ? up : 1);
+  std::vector<uint32_t> bits(up > 0 ? up : 1);
+  for (int i = 0; i < up; ++i) {
+    const int32_t* q = hits_all + 5 * (size_t)i;
+    if (q[1] < 0 || q[1] >= s->cap || q[2] < -1 || q[2] >= s->cap)
+      return fail(s, CORAL_E_INVALID, "hit with a genome slot out of range");
+    h[i] = make_int4(q[0], q[1], q[2], q[3]);
+    bits[i] = (uint32_t)q[4];
+  }
+  int c[8] = {counts_all[0], 0, 0, counts_all[1], counts_all[2], 0, 0, 0};
+  CK(s, cudaMemcpyAsync(s->count, flags.data(), sizeof(int32_t) * s->cap, cudaMemcpyHostToDevice, s->stream));
+  if (up > 0) {
+    CK(s, cudaMemcpyAsync(s->hits, h.data(), sizeof(int4) * up, cudaMemcpyHostToDevice, s->stream));
+    CK(s, cudaMemcpyAsync(s->hitbits, bits.data(), sizeof(uint32_t) * up, cudaMemcpyHostToDevice, s->stream));
+  }
+  CK(s, cudaMemcpyAsync(s->counters, c, sizeof(c), cudaMemcpyHostToDevice, s->stream));
+  RadiationArgs r = radiation_args(s, s->t - 1);
+  r.max_hits = up;                       // only the listed hits can be assigned
+  CK(s, launch_radiation_apply(r, s->stream));
+  CK(s, cudaStreamSynchronize(s->stream));   // the host vectors above are released on return
+  return check_status(s);
 }
 
 int coral_sync(coral_substrate* s) {

@@ -247,6 +247,10 @@ struct RadiationArgs {
   int W, H;
   long long N;
   int32_t* G;                 // current state's G (rewritten in place for the children)
+  // the cells radiation acts on: [j0, j0 + n_own) of G, whose global cell ids (the Philox
+  // counter and the hit order) start at gid0; the whole grid (0, N, 0) unless the substrate is
+  // one row slab of a larger world
+  long long j0, n_own, gid0;
   GenomeArgs g;
   uint32_t thr_mut, thr_merge;
   float sigma;
@@ -267,6 +271,17 @@ struct RadiationArgs {
   coral_stats* rec;           // stats record of this step
 };
 cudaError_t launch_radiation(const RadiationArgs& r, cudaStream_t st);
+// The two halves of launch_radiation for a row slab: the scan leaves the liveness flags of the
+// own cells in r.count and the hits (global cell ids, in cell order) in r.hits / r.hitbits with
+// their count in r.counters[0]; the apply takes global liveness flags in r.count and the global
+// hit list in r.hits / r.hitbits / r.counters[0] (with the event counts in r.counters[3..4]),
+// assigns the lowest free slots to the hits in order, writes the children and the G of the own
+// cells among them, and regenerates the new slots' nets.
+cudaError_t launch_radiation_scan(const RadiationArgs& r, cudaStream_t st);
+cudaError_t launch_radiation_apply(const RadiationArgs& r, cudaStream_t st);
+// FP64 totals (E, I, C0..C3) of cells [j0, j0 + n) of the six contiguous sensor planes at E,
+// fixed order, into out[6] (device)
+cudaError_t launch_row_totals(const float* E, long long N, long long j0, long long n, double* out, cudaStream_t st);
 int radiation_blocks(long long N);
 int radiation_threads();   // threads per radiation block (one hit-mask byte each)
 

@@ -166,7 +166,7 @@ struct Hit {
 
 __device__ __forceinline__ Hit radiation_hit(const RadiationArgs& r, long long j) {
   Hit h = {false, false, false, 0, -1, 0};
-  const uint32_t cell = (uint32_t)j;
+  const uint32_t cell = (uint32_t)(j - r.j0 + r.gid0);       // global cell id
   const uint32_t cap = (uint32_t)r.g.capacity;
   if ((uint32_t)r.G[j] >= cap) return h;              // invalid GenomeIndex: never a parent
   if (r.thr_mut) h.mut = draw(cell, r.step, 0, 0, r.world, r.seed).x < r.thr_mut;
@@ -213,12 +213,12 @@ __device__ __forceinline__ int block_exscan(int v, int& total) {
 }
 
 __global__ void __launch_bounds__(kRadThreads) k_rad_count(RadiationArgs r) {
-  const long long base = (long long)blockIdx.x * kRadTile + (long long)threadIdx.x * kRadPerThread;
+  const long long base = r.j0 + (long long)blockIdx.x * kRadTile + (long long)threadIdx.x * kRadPerThread;
   int nh = 0, nm = 0, ng = 0;
   uint32_t mask = 0;
   for (int i = 0; i < kRadPerThread; ++i) {
     const long long j = base + i;
-    if (j >= r.N) break;
+    if (j >= r.j0 + r.n_own) break;
     const Hit h = radiation_hit(r, j);
     nh += h.hit;
     nm += h.mut;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(1024) k_scan(const int32_t* in, int32_t* out, 
 // Writes the hits in cell order. The counting pass left each thread's hit bits in the mask, so
 // only hit cells (about p_mut + p_merge of them) draw their Philox numbers again here.
 __global__ void __launch_bounds__(kRadThreads) k_rad_emit(RadiationArgs r) {
-  const long long base = (long long)blockIdx.x * kRadTile + (long long)threadIdx.x * kRadPerThread;
+  const long long base = r.j0 + (long long)blockIdx.x * kRadTile + (long long)threadIdx.x * kRadPerThread;
   uint32_t mask = r.hitmask[(long long)blockIdx.x * kRadThreads + threadIdx.x];
   int tot;
   int pos = r.blockoff[blockIdx.x] + block_exscan(__popc(mask), tot);
@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kRadThreads) k_rad_emit(RadiationArgs r) {
     mask &= mask - 1;
     const Hit h = radiation_hit(r, base + i);
     if (pos < r.max_hits) {
-      r.hits[pos] = make_int4((int)(base + i), h.g, h.merge ? h.gp : -1, (h.mut ? 1 : 0) | (h.merge ? 2 : 0));
+      r.hits[pos] = make_int4((int)(base + i - r.j0 + r.gid0), h.g, h.merge ? h.gp : -1, (h.mut ? 1 : 0) | (h.merge ? 2 : 0));
       r.hitbits[pos] = h.bits;
     }
     ++pos;
@@ -424,7 +424,8 @@ __global__ void __launch_bounds__(128) k_rad_assign(RadiationArgs r) {
 #pragma unroll
     for (int k = 0; k < kGenes; ++k) dst[k] = c[k];
     r.g.parent[slot] = h.y;
-    r.G[h.x] = slot;
+    const long long lj = (long long)h.x - r.gid0 + r.j0;     // the hit cell in this grid, if own
+    if (lj >= r.j0 && lj < r.j0 + r.n_own) r.G[lj] = slot;
     r.newslots[i] = slot;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -700,18 +701,23 @@ cudaError_t launch_validate_state(const int32_t* G, const uint8_t* R, long long 
   return cudaGetLastError();
 }
 
-cudaError_t launch_radiation(const RadiationArgs& r, cudaStream_t st) {
-  const int nblk = radiation_blocks(r.N);
+cudaError_t launch_radiation_scan(const RadiationArgs& r, cudaStream_t st) {
+  const int nblk = radiation_blocks(r.n_own);
   cudaError_t e;
   if ((e = cudaMemsetAsync(r.count, 0, sizeof(int32_t) * r.g.capacity, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(r.counters, 0, sizeof(int) * 8, st)) != cudaSuccess) return e;
   if (r.g.capacity <= 32 * kLiveMaxWords)
-    k_live<<<1024, kLiveThreads, 0, st>>>(r.G, r.N, r.g.capacity, r.count);
+    k_live<<<1024, kLiveThreads, 0, st>>>(r.G + r.j0, r.n_own, r.g.capacity, r.count);
   else
-    k_live_plain<<<1024, 256, 0, st>>>(r.G, r.N, r.g.capacity, r.count);
+    k_live_plain<<<1024, 256, 0, st>>>(r.G + r.j0, r.n_own, r.g.capacity, r.count);
   k_rad_count<<<nblk, kRadThreads, 0, st>>>(r);
   k_scan<<<1, 1024, 0, st>>>(r.blockcnt, r.blockoff, nblk, &r.counters[0]);
   k_rad_emit<<<nblk, kRadThreads, 0, st>>>(r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_radiation_apply(const RadiationArgs& r, cudaStream_t st) {
+  cudaError_t e;
   {
     // blockcnt / blockoff are free again once the hits are emitted; the slot passes reuse them
     RadiationArgs f = r;
@@ -723,6 +729,51 @@ cudaError_t launch_radiation(const RadiationArgs& r, cudaStream_t st) {
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = launch_cppn_generate(r.g, r.newslots, &r.counters[2], 0, st)) != cudaSuccess) return e;
   return launch_bf16_pack(r.g, r.newslots, &r.counters[2], 0, st);
+}
+
+cudaError_t launch_radiation(const RadiationArgs& r, cudaStream_t st) {
+  cudaError_t e = launch_radiation_scan(r, st);
+  return e != cudaSuccess ? e : launch_radiation_apply(r, st);
+}
+
+namespace {
+// FP64 totals of a cell range: each block sums a contiguous chunk (doubles, a fixed tree), one
+// partial per block and plane; block 0 of a second launch adds the partials in block order.
+constexpr int kTotBlocks = 256;
+__global__ void __launch_bounds__(256) k_row_totals(const float* E, long long N, long long j0, long long n,
+                                                    double* part) {
+  __shared__ double red[256];
+  const long long per = (n + kTotBlocks - 1) / kTotBlocks;
+  const long long c0 = j0 + (long long)blockIdx.x * per;
+  const long long c1 = c0 + per < j0 + n ? c0 + per : j0 + n;
+  for (int p = 0; p < 6; ++p) {
+    double s = 0.0;
+    for (long long j = c0 + threadIdx.x; j < c1; j += 256) s += (double)E[(long long)p * N + j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[p * kTotBlocks + blockIdx.x] = red[0];
+    __syncthreads();
+  }
+}
+__global__ void k_row_totals_final(const double* part, double* out) {
+  const int p = threadIdx.x;
+  if (p < 6) {
+    double s = 0.0;
+    for (int b = 0; b < kTotBlocks; ++b) s += part[p * kTotBlocks + b];
+    out[p] = s;
+  }
+}
+}  // namespace
+
+cudaError_t launch_row_totals(const float* E, long long N, long long j0, long long n, double* out, cudaStream_t st) {
+  // out must have room for 6 + 6 * kTotBlocks doubles: the partials follow the six totals
+  k_row_totals<<<kTotBlocks, 256, 0, st>>>(E, N, j0, n, out + 6);
+  k_row_totals_final<<<1, 32, 0, st>>>(out + 6, out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_bucket(const SortArgs& a, cudaStream_t st) {
