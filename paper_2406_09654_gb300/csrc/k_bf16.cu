@@ -1,17 +1,17 @@
 // BF16 tensor-core network (pass 1) on tcgen05: each CTA takes a contiguous run of 32x4-cell
-// tiles of the torus, then chunks of tiles from a shared pool. A tile's one-cell halo of the six sensor channels comes into shared memory
-// by one TMA box copy (cp.async where the halo wraps around the torus); the CTA turns it into
-// BF16 cell records and takes each cell's own E, I and flow denominator from it, after which the
-// buffer is free and the next tile's copy overlaps this tile's network. From the records it
-// builds the 128 x 64 BF16 input tile (the rotation-ordered 3x3 neighbourhood of every cell, K
-// index 6*rank + channel, a constant 1 at K = 54 that carries the layer-1 bias) and runs the
-// genome nets on the tensor cores with FP32 accumulation in TMEM: one 128 x H x 64 MMA for
-// layer 1 (both operands in shared memory), tanh in the epilogue with the BF16 hidden tile
-// written back into the consumed TMEM columns, one 128 x 16 x H MMA for layer 2 that reads
-// its A operand from TMEM. A tile with several genomes runs
-// one round per genome (the rows of other genomes are computed and discarded); a cell's
-// actuator epilogue (communication, invest/liquidate, exploration, flow quotient) runs in
-// registers in the round that computes its outputs.
+// tiles of the torus, then chunks of tiles from a shared pool. A tile's one-cell halo of the six
+// sensor channels comes into shared memory by one TMA box copy (cp.async where the halo wraps
+// around the torus). Every thread builds its cell's row of the 128 x 64 BF16 input tile straight
+// from that stage (the rotation-ordered 3x3 neighbourhood, K index 6*rank + channel, a constant
+// 1 at K = 54 that carries the layer-1 bias) and takes its own E, I and flow denominator from
+// it; after one CTA barrier the stage is free and the next tile's copy overlaps this tile's
+// network. The genome nets run on the tensor cores with FP32 accumulation in TMEM: one
+// 128 x H x 64 MMA for layer 1 (both operands in shared memory; the genome's BF16 blob arrives
+// by one bulk copy when it changes), tanh in the epilogue with the BF16 hidden tile written back
+// into the consumed TMEM columns, one 128 x 16 x H MMA for layer 2 that reads its A operand from
+// TMEM. A tile with several genomes runs one round per genome (the rows of other genomes are
+// computed and discarded); a cell's actuator epilogue (communication, invest/liquidate,
+// exploration, flow quotient) runs in registers in the round that computes its outputs.
 #include <cudaTypedefs.h>
 #include <math.h>
 #include <string.h>
@@ -52,13 +52,12 @@ constexpr int kOffA = 0;                                  // 128 x 128 B: input 
 constexpr int kOffW = 16384;                              // genome blob (<= 10368 B at H = 64)
 // stage: float32 [6 channels][6 rows][40 columns], halo column hx at 3 + hx (the TMA box starts
 // 4 cells left of the tile so its x coordinate stays 16-byte aligned). One buffer: it is free
-// again once the tile's records and each thread's own E, I and flow denominator are taken from
-// it, so the next tile's copy overlaps the current tile's network rounds.
+// again once every thread has built its input row and taken its own E, I and flow denominator
+// from it, so the next tile's copy overlaps the current tile's network rounds.
 constexpr int kStageW = kTileW + 8, kStageCh = kStageW * kHaloH;  // 240 floats per channel
 constexpr int kStageBytes = 6 * kStageCh * 4;             // 5760
 constexpr int kOffStage = kOffW + 10368;                  // 128-byte aligned
-constexpr int kOffRec = kOffStage + kStageBytes;          // 204 x 16 B BF16 cell records
-constexpr int kOffG = kOffRec + kHaloCells * 16;          // int32 [128]
+constexpr int kOffG = kOffStage + kStageBytes;            // int32 [128]
 constexpr int kOffMisc = kOffG + 512;                     // mbarrier, TMEM slot, flags
 constexpr int kSmemBytes = kOffMisc + 128 + 1024;         // + alignment slack
 
@@ -89,14 +88,14 @@ __device__ __forceinline__ int fold(int v, int n, bool small) {
   return v < 0 ? v + n : (v >= n ? v - n : v);
 }
 
-// Record-index offset (dy * 34 + dx) of kernel ranks 1..8 for rotation r, one signed byte per
-// rank (rank p in bits 8(p-1)..8p-1), from the same octant tables as the FP32 path.
-__host__ __device__ constexpr unsigned long long rank_offsets(int r) {
+// Stage-index offset (dy * kStageW + dx) of kernel ranks 1..8 for rotation r, one signed byte
+// per rank (rank p in bits 8(p-1)..8p-1).
+__host__ __device__ constexpr unsigned long long stage_offsets(int r) {
   unsigned long long v = 0;
   for (int p = 1; p < 9; ++p) {
     const int o = (2 * r + rank_delta(p)) & 7;
     const int dx = (int)((0x1A9u >> (2 * o)) & 3u) - 1, dy = (int)((0x1A90u >> (2 * o)) & 3u) - 1;
-    v |= (unsigned long long)(uint8_t)(int8_t)(dy * kHaloW + dx) << (8 * (p - 1));
+    v |= (unsigned long long)(uint8_t)(int8_t)(dy * kStageW + dx) << (8 * (p - 1));
   }
   return v;
 }
@@ -138,6 +137,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   uint8_t* base = smem_raw + (base_s - raw_s);
   int32_t* sG = reinterpret_cast<int32_t*>(base + kOffG);
   uint64_t* mbar = reinterpret_cast<uint64_t*>(base + kOffMisc);
+  uint64_t* w_bar = reinterpret_cast<uint64_t*>(base + kOffMisc + 96);    // bulk copy of a genome blob
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(base + kOffMisc + 8);
   unsigned* ballots = reinterpret_cast<unsigned*>(base + kOffMisc + 16);      // [2][4] pending rows
   uint64_t* halo_bar = reinterpret_cast<uint64_t*>(base + kOffMisc + 48);     // the stage's TMA barrier
@@ -151,7 +151,6 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   const int W = a.W, Hh = a.H;
   constexpr int H = kH;
   constexpr int N1 = H ? H : 16;
-  const uint32_t rec_s = base_s + kOffRec;
   const uint32_t w_s = base_s + kOffW;
   const uint32_t a_s = base_s + kOffA;
 
@@ -161,6 +160,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   }
   if (tid == 0) {
     tc::mbar_init(mbar, 1);
+    tc::mbar_init(w_bar, 1);
     tc::mbar_init(halo_bar, 1);
     tc::fence_barrier_init();
   }
@@ -171,7 +171,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   const uint32_t t_lane = tmem + ((uint32_t)(warp * 32) << 16);
   const uint32_t idesc1 = tc::idesc_bf16_f32(128, N1);
   const uint32_t idesc2 = tc::idesc_bf16_f32(128, 16);
-  uint32_t phase = 0;
+  uint32_t phase = 0, w_phase = 0;
 
   if (lane == 0) {                                    // this warp's fixed-point sums of C'
 #pragma unroll
@@ -248,7 +248,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   while (cur >= 0) {
     const int x0 = tx * kTileW, y0 = ty * kTileH;
     // the next tile: the next one of this run, or the first of a newly claimed pool chunk
-    // (claimed now, read after the records barrier; two slots, so that a slow thread still
+    // (claimed now, read after the input-tile barrier; two slots, so that a slow thread still
     // reading the last claim never sees it overwritten)
     const bool claim = cur + 1 >= run_end;
     if (tid == 0) {
@@ -278,13 +278,27 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     }
     sG[tid] = g;
     const float* stage = reinterpret_cast<const float*>(base + kOffStage);
-    // BF16 records: the 6 channels of each halo cell in one 16-byte slot
-    for (int c = tid; c < kHaloCells; c += kThreads) {
-      const int hy = c / kHaloW;
-      const float* s = stage + hy * kStageW + (c - hy * kHaloW) + 3;
-      tc::sts128(rec_s + c * 16, tc::pack_bf16x2(s[0], s[kStageCh]),
-                 tc::pack_bf16x2(s[2 * kStageCh], s[3 * kStageCh]),
-                 tc::pack_bf16x2(s[4 * kStageCh], s[5 * kStageCh]), 0u);
+    // this cell's input row, straight from the stage: chunk p = the 6 BF16 channels of kernel
+    // rank p (p < 8) and a spare word with rank 8's channels (p < 3) or the bias 1.0 (p = 3);
+    // 128-byte swizzle. Rows of cells outside the grid get what the stage holds there and are
+    // discarded.
+    {
+      const uint32_t row_s = a_s + tid * 128;
+      const uint32_t t7 = tid & 7;
+      const int sc = (ly + 1) * kStageW + lx + 4;
+      const unsigned long long offs = r == 0 ? stage_offsets(0) : r == 1 ? stage_offsets(1)
+                                    : r == 2 ? stage_offsets(2) : stage_offsets(3);
+      const float* s8 = stage + sc + (int)(int8_t)(uint8_t)(offs >> 56);
+      const uint32_t w8[3] = {tc::pack_bf16x2(s8[0], s8[kStageCh]), tc::pack_bf16x2(s8[2 * kStageCh], s8[3 * kStageCh]),
+                              tc::pack_bf16x2(s8[4 * kStageCh], s8[5 * kStageCh])};
+#pragma unroll
+      for (int p = 0; p < 8; ++p) {
+        const float* sp = stage + sc + (p == 0 ? 0 : (int)(int8_t)(uint8_t)(offs >> (8 * (p - 1))));
+        const uint32_t w4 = p < 3 ? w8[p] : (p == 3 ? 0x3F80u : 0u);
+        tc::sts128(row_s + (((uint32_t)p ^ t7) << 4), tc::pack_bf16x2(sp[0], sp[kStageCh]),
+                   tc::pack_bf16x2(sp[2 * kStageCh], sp[3 * kStageCh]), tc::pack_bf16x2(sp[4 * kStageCh], sp[5 * kStageCh]),
+                   w4);
+      }
     }
     // this cell's E and I and the FP64 sum S of its 4 neighbours' I (N, E, S, W), rounded once
     float Ec, Ic, Sf;
@@ -311,8 +325,8 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       const unsigned m = __ballot_sync(0xffffffffu, !done && g == staged);   // rows of the staged genome
       if (lane == 0) match[warp] = m;
     }
-    tc::fence_proxy_async();                          // stage reads before the next tile's copy
-    if (__syncthreads_or(bad)) {                      // records and the first ballots visible
+    tc::fence_proxy_async();                          // input rows for the MMA; stage reads before the next copy
+    if (__syncthreads_or(bad)) {                      // input tile and the first ballots visible
       timed_out = true;
       break;
     }
@@ -331,8 +345,6 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
       }
       prefetch(tx * kTileW, ty * kTileH);
     }
-    const int hc = (ly + 1) * kHaloW + (lx + 1);
-    const uint32_t row_s = a_s + tid * 128;
     // actuator epilogue and pass-1 stores of this thread's cell, in the round that finishes it
     auto finish = [&](const float* act, const float* zo) {
       CellOut o;
@@ -349,10 +361,11 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     // One tensor-core round per genome present in the tile: first the genome whose blob is
     // already staged, if the tile has cells of it, then the first pending row's genome.
     // The input tile in shared memory survives the rounds (the hidden tile lives in TMEM), so
-    // it is built once per tile. Each round publishes the
-    // rows still pending after it in the other ballot buffer before its first barrier, so the
-    // tile ends without a further barrier; the MMAs' completion is awaited by every thread on
-    // the mbarrier, not through a CTA barrier.
+    // it is built once per tile. Each round publishes the rows still pending after it in the
+    // other ballot buffer before its hidden-tile barrier, so a single-genome tile costs two CTA
+    // barriers (input tile, hidden tile); a later round starts with one more, after which the
+    // last round's TMEM columns and b2 may be overwritten. The MMAs' completion is awaited by
+    // every thread on the mbarrier, not through a CTA barrier.
     bool first_round = true;
     while (true) {
       const uint4 bl = *reinterpret_cast<const uint4*>(ballots + 4 * rb);
@@ -364,62 +377,37 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
         if (mt.x | mt.y | mt.z | mt.w) gs = staged;
       }
       if (gs < 0) break;
-      if (staged != gs) {                             // stage this genome's BF16 blob
-        // in a later round of a tile, slower threads may still be reading the previous
-        // genome's b2 (no barrier since): wait for them (rare: tiles with several genomes)
-        if (!first_round) __syncthreads();
-        // an out-of-range GenomeIndex (loaded, reported as invalid, not yet read back) runs
-        // slot 0's net instead of reading outside the genome table
-        const int gsafe = (unsigned)gs < (unsigned)a.capacity ? gs : 0;
-        const uint4* src = reinterpret_cast<const uint4*>(a.nets16 + (long long)gsafe * a.blob_bytes);
-        const int n16 = a.blob_bytes >> 4;             // <= 648 = 6 x 108 per thread slot
-#pragma unroll
-        for (int half = 0; half < 2; ++half) {
-          uint4 v[3];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const int i = tid + (3 * half + k) * kThreads;
-            if (i < n16) v[k] = __ldg(src + i);
-          }
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            const int i = tid + (3 * half + k) * kThreads;
-            if (i < n16) tc::sts128(w_s + i * 16, v[k].x, v[k].y, v[k].z, v[k].w);
-          }
-        }
-        staged = gs;
-      }
-      // this cell's input row: chunk p = the record of kernel rank p (p < 8) whose spare 4th
-      // word carries rank 8's channels (p < 3) or the bias 1.0 (p = 3); 128-byte swizzle.
-      // Rows of cells outside the grid are left as they are: their outputs are discarded.
-      if (first_round && valid) {
-        const uint32_t c_s = rec_s + hc * 16;
-        const unsigned long long offs = r == 0 ? rank_offsets(0) : r == 1 ? rank_offsets(1)
-                                      : r == 2 ? rank_offsets(2) : rank_offsets(3);
-        const uint4 r8 = tc::lds128(c_s + (int)(int8_t)(uint8_t)(offs >> 56) * 16);
-        const uint32_t t7 = tid & 7;
-        uint4 rc = tc::lds128(c_s);
-        tc::sts128(row_s + ((0u ^ t7) << 4), rc.x, rc.y, rc.z, r8.x);
-#pragma unroll
-        for (int p = 1; p < 8; ++p) {
-          const int off = (int)(int8_t)(uint8_t)(offs >> (8 * (p - 1)));
-          rc = tc::lds128(c_s + off * 16);
-          const uint32_t w4 = p == 1 ? r8.y : (p == 2 ? r8.z : (p == 3 ? 0x3F80u : 0u));
-          tc::sts128(row_s + (((uint32_t)p ^ t7) << 4), rc.x, rc.y, rc.z, w4);
+      // a later round of a tile: every thread has read the last round's layer-2 outputs (TMEM)
+      // and b2 (shared memory) before the new layer-1 MMA or the restaging overwrites them
+      if (!first_round) {
+        tc::fence_proxy_async();                      // b2 reads before a bulk copy over them
+        if (__syncthreads_or(bad)) {
+          timed_out = true;
+          break;
         }
       }
+      const bool restage = staged != gs;
       const bool mine = !done && g == gs;
       {
         const unsigned b = __ballot_sync(0xffffffffu, !done && !mine);   // pending after this round
         if (lane == 0) ballots[4 * (rb ^ 1) + warp] = b;
       }
-      tc::fence_proxy_async();
-      if (__syncthreads_or(bad)) {
-        timed_out = true;
-        break;
+      if constexpr (H == 0) {                         // no hidden-tile barrier: this one publishes
+        if (__syncthreads_or(bad)) {                  // the ballots before the next round reads them
+          timed_out = true;
+          break;
+        }
       }
       if (tid == 0) {
         tc::tc_fence_after();
+        if (restage) {                                // this genome's BF16 blob, one bulk copy
+          // an out-of-range GenomeIndex (loaded, reported as invalid, not yet read back) runs
+          // slot 0's net instead of reading outside the genome table
+          const int gsafe = (unsigned)gs < (unsigned)a.capacity ? gs : 0;
+          tc::mbar_expect_tx(w_bar, (uint32_t)a.blob_bytes);
+          tc::bulk_load(w_s, a.nets16 + (long long)gsafe * a.blob_bytes, (uint32_t)a.blob_bytes, w_bar);
+          if (!tc::mbar_wait(w_bar, w_phase, kWaitCycles)) bad = true;
+        }
         const uint64_t ad = tc::sdesc_sw128(a_s), bd = tc::sdesc_sw128(w_s);
 #pragma unroll
         for (int k = 0; k < 4; ++k) tc::mma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc1, k > 0);
@@ -473,6 +461,9 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
         float v[16];
         tc::tmem_ld16(t_lane + kD2Col, v);
         tc::tmem_wait_ld();
+        if (restage) {                                // the blob's bytes seen by this thread too
+          if (!tc::mbar_wait(w_bar, w_phase, kWaitCycles)) bad = true;
+        }
         if (mine) {
           const float* b2 = reinterpret_cast<const float*>(base + kOffW + bf16_b2_off(H));
           float act[kOut];
@@ -485,6 +476,10 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
         }
       }
       tc::tc_fence_before();
+      if (restage) {
+        staged = gs;
+        w_phase ^= 1u;
+      }
       if (mine) done = true;
       first_round = false;
       rb ^= 1;
