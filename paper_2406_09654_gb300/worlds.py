@@ -234,7 +234,8 @@ def make_world(preset: str | None = None, seed: int = 0, **overrides) -> World:
 
     layout = cfg.get("layout", "voronoi")
     if layout == "voronoi":
-        G = _torus_voronoi(width, height, n, rng)
+        # the same layout; the k-d tree search for large grids (equal to the plain one, tested)
+        G = (_torus_voronoi_tree if width * height * n > 10**8 else _torus_voronoi)(width, height, n, rng)
     elif layout == "hilbert_zipf":
         G = _hilbert_zipf(width, height, n, float(cfg.get("zipf_s", 1.2)))
     elif layout == "random":
