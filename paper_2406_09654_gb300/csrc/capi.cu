@@ -27,7 +27,9 @@ struct JobPipe {
 struct coral_substrate {
   coral_params p;
   int W = 0, H = 0;
-  long long N = 0;
+  int P = 0;                    // row pitch of the planes in cells (W rounded up to a multiple of 4)
+  long long N = 0;              // plane length H * P
+  long long NL = 0;             // torus cells W * H
   int cap = 0;
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -120,6 +122,7 @@ StepArgs step_args(const coral_substrate* s) {
   a.W = s->W;
   a.H = s->H;
   a.N = s->N;
+  a.P = s->P;
   a.hidden = s->p.hidden;
   a.rotation = s->p.rotation;
   a.k_inv = s->p.k_inv;
@@ -194,7 +197,8 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
   if (!p || !out) return fail(nullptr, CORAL_E_INVALID, "NULL argument");
   *out = nullptr;
   if (width < 3 || height < 3) return fail(nullptr, CORAL_E_INVALID, "width and height must be >= 3");
-  if ((long long)width * height >= (1LL << 31)) return fail(nullptr, CORAL_E_INVALID, "width * height must be < 2^31");
+  if ((long long)row_pitch(width) * height >= (1LL << 31))
+    return fail(nullptr, CORAL_E_INVALID, "width (rounded up to a multiple of 4) * height must be < 2^31");
   if (genome_capacity < 1 || genome_capacity > (1 << 24))
     return fail(nullptr, CORAL_E_INVALID, "genome_capacity must be in [1, 2^24]");
   if (!valid_hidden(p->hidden)) return fail(nullptr, CORAL_E_INVALID, "hidden must be 0, 16, 32, 48 or 64");
@@ -213,7 +217,9 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
   s->p = *p;
   s->W = width;
   s->H = height;
-  s->N = (long long)width * height;
+  s->P = row_pitch(width);
+  s->N = (long long)height * s->P;
+  s->NL = (long long)width * height;
   s->cap = genome_capacity;
   s->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
   int rc = CORAL_OK;
@@ -262,7 +268,15 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
       rc = fail(s, CORAL_E_OOM, "device allocation failed");
       break;
     }
-    if ((e = cudaMemset(s->status, 0, 4 * sizeof(int))) != cudaSuccess ||
+    // row padding: G = -1 (no genome), R = 0, floats 0, in both state buffers; loads and reads
+    // copy the torus columns only, and the kernels keep the padding as it is
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      if ((e = cudaMemset(s->st[b].E, 0, sizeof(float) * 6 * N)) == cudaSuccess &&
+          (e = cudaMemset(s->st[b].G, 0xFF, sizeof(int32_t) * N)) == cudaSuccess)
+        e = cudaMemset(s->st[b].R, 0, (size_t)N);
+    }
+    if (e != cudaSuccess ||
+        (e = cudaMemset(s->status, 0, 4 * sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(s->sched, 0, 2 * sizeof(int))) != cudaSuccess ||
         (e = cudaMemset(s->ring, 0, kRing * sizeof(coral_stats))) != cudaSuccess ||
         (e = cudaMemset(s->g.parent, 0xFF, sizeof(int32_t) * genome_capacity)) != cudaSuccess ||
@@ -274,8 +288,8 @@ int coral_substrate_create(const coral_params* p, int32_t width, int32_t height,
     }
     s->grid1 = p->path == CORAL_NET_BF16_GROUPED ? pass1_bf16_grid(s->sms) : pass1_fp32_grid(s->sms);
     if (p->path == CORAL_NET_BF16_GROUPED)
-      s->tmap_ok = encode_sensor_tmap(&s->tmap[0], s->st[0].E, width, height) &&
-                   encode_sensor_tmap(&s->tmap[1], s->st[1].E, width, height);
+      s->tmap_ok = encode_sensor_tmap(&s->tmap[0], s->st[0].E, width, height, s->P) &&
+                   encode_sensor_tmap(&s->tmap[1], s->st[1].E, width, height, s->P);
     s->grid2 = pass2_grid(s->sms);
     if (s->grid1 < 1) {
       rc = fail(s, CORAL_E_CUDA, "the BF16 tensor-core kernel cannot be launched on this device");
@@ -316,15 +330,17 @@ int coral_substrate_destroy(coral_substrate* s) {
 int coral_state_load(coral_substrate* s, const float* E, const float* I, const float* C, const int32_t* G,
                      const uint8_t* R, int src_on_device) {
   if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
-  const long long N = s->N;
   const Planes& d = s->st[s->cur];
   const cudaMemcpyKind k = kind_in(src_on_device);
-  if (E) CK(s, cudaMemcpyAsync(d.E, E, sizeof(float) * N, k, s->stream));
-  if (I) CK(s, cudaMemcpyAsync(d.I, I, sizeof(float) * N, k, s->stream));
-  if (C) CK(s, cudaMemcpyAsync(d.C, C, sizeof(float) * 4 * N, k, s->stream));
-  if (G) CK(s, cudaMemcpyAsync(d.G, G, sizeof(int32_t) * N, k, s->stream));
-  if (R) CK(s, cudaMemcpyAsync(d.R, R, N, k, s->stream));
-  if (G || R) CK(s, launch_validate_state(G ? d.G : nullptr, R ? d.R : nullptr, N, s->cap, s->status, s->stream));
+  const size_t W = (size_t)s->W, H = (size_t)s->H, P = (size_t)s->P;
+  // packed rows of W cells in, pitched rows of P cells on the device (the padding untouched)
+  if (E) CK(s, cudaMemcpy2DAsync(d.E, 4 * P, E, 4 * W, 4 * W, H, k, s->stream));
+  if (I) CK(s, cudaMemcpy2DAsync(d.I, 4 * P, I, 4 * W, 4 * W, H, k, s->stream));
+  if (C) CK(s, cudaMemcpy2DAsync(d.C, 4 * P, C, 4 * W, 4 * W, 4 * H, k, s->stream));
+  if (G) CK(s, cudaMemcpy2DAsync(d.G, 4 * P, G, 4 * W, 4 * W, H, k, s->stream));
+  if (R) CK(s, cudaMemcpy2DAsync(d.R, P, R, W, W, H, k, s->stream));
+  if (G || R)
+    CK(s, launch_validate_state(G ? d.G : nullptr, R ? d.R : nullptr, s->W, s->H, s->P, s->cap, s->status, s->stream));
   // host sources may be pinned: the copies must finish before the caller regains the buffers
   if (!src_on_device) CK(s, cudaStreamSynchronize(s->stream));
   s->t = 0;
@@ -389,9 +405,10 @@ RadiationArgs radiation_args(coral_substrate* s, long long t) {
   r.W = s->W;
   r.H = s->H;
   r.N = s->N;
+  r.P = s->P;
   r.G = s->st[s->cur].G;
-  r.j0 = s->slab ? (long long)s->row_lo * s->W : 0;
-  r.n_own = s->slab ? (long long)(s->row_hi - s->row_lo) * s->W : s->N;
+  r.j0 = s->slab ? (long long)s->row_lo * s->P : 0;
+  r.n_own = s->slab ? (long long)(s->row_hi - s->row_lo) * s->P : s->N;
   r.gid0 = s->slab ? s->gid0 : 0;
   r.g = s->g;
   r.thr_mut = hit_threshold(s->p.p_mut);
@@ -459,7 +476,7 @@ namespace {
 int jobs_setup(coral_substrate* s) {
   JobPipe& jp = s->jobs;
   if (jp.ready) return CORAL_OK;
-  const size_t bytes = (size_t)kStateBytesPerCell * (size_t)s->N;
+  const size_t bytes = (size_t)kStateBytesPerCell * (size_t)s->NL;
   for (int b = 0; b < 2; ++b) {
     CK(s, dalloc(s, &jp.in[b], bytes));
     CK(s, dalloc(s, &jp.out[b], bytes));
@@ -478,19 +495,21 @@ int jobs_setup(coral_substrate* s) {
 int enqueue_job(coral_substrate* s, int k, const void* src, void* dst, int32_t n_steps, int64_t t0) {
   JobPipe& jp = s->jobs;
   const int b = k & 1;
-  const long long N = s->N;
+  const long long N = s->NL;                        // packed cells of a job's state
   const size_t bytes = (size_t)kStateBytesPerCell * (size_t)N;
+  const size_t W = (size_t)s->W, H = (size_t)s->H, P = (size_t)s->P;
   if (k >= 2) CK(s, cudaStreamWaitEvent(jp.s_in, jp.in_free[b], 0));
   CK(s, cudaMemcpyAsync(jp.in[b], src, bytes, cudaMemcpyHostToDevice, jp.s_in));
   CK(s, cudaEventRecord(jp.h2d_done[b], jp.s_in));
   CK(s, cudaStreamWaitEvent(s->stream, jp.h2d_done[b], 0));
   {
     const Planes& d = s->st[s->cur];
-    CK(s, cudaMemcpyAsync(d.E, jp.in[b], sizeof(float) * 6 * N, cudaMemcpyDeviceToDevice, s->stream));
-    CK(s, cudaMemcpyAsync(d.G, jp.in[b] + 24 * N, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s->stream));
-    CK(s, cudaMemcpyAsync(d.R, jp.in[b] + 28 * N, (size_t)N, cudaMemcpyDeviceToDevice, s->stream));
+    // the six float planes are 6H packed rows in, 6H pitched rows on the device
+    CK(s, cudaMemcpy2DAsync(d.E, 4 * P, jp.in[b], 4 * W, 4 * W, 6 * H, cudaMemcpyDeviceToDevice, s->stream));
+    CK(s, cudaMemcpy2DAsync(d.G, 4 * P, jp.in[b] + 24 * N, 4 * W, 4 * W, H, cudaMemcpyDeviceToDevice, s->stream));
+    CK(s, cudaMemcpy2DAsync(d.R, P, jp.in[b] + 28 * N, W, W, H, cudaMemcpyDeviceToDevice, s->stream));
     CK(s, cudaEventRecord(jp.in_free[b], s->stream));
-    CK(s, launch_validate_state(d.G, d.R, N, s->cap, s->status, s->stream));
+    CK(s, launch_validate_state(d.G, d.R, s->W, s->H, s->P, s->cap, s->status, s->stream));
   }
   s->t = t0;
   for (int i = 0; i < n_steps; ++i) {
@@ -500,9 +519,9 @@ int enqueue_job(coral_substrate* s, int k, const void* src, void* dst, int32_t n
   if (k >= 2) CK(s, cudaStreamWaitEvent(s->stream, jp.out_free[b], 0));
   {
     const Planes& d = s->st[s->cur];
-    CK(s, cudaMemcpyAsync(jp.out[b], d.E, sizeof(float) * 6 * N, cudaMemcpyDeviceToDevice, s->stream));
-    CK(s, cudaMemcpyAsync(jp.out[b] + 24 * N, d.G, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, s->stream));
-    CK(s, cudaMemcpyAsync(jp.out[b] + 28 * N, d.R, (size_t)N, cudaMemcpyDeviceToDevice, s->stream));
+    CK(s, cudaMemcpy2DAsync(jp.out[b], 4 * W, d.E, 4 * P, 4 * W, 6 * H, cudaMemcpyDeviceToDevice, s->stream));
+    CK(s, cudaMemcpy2DAsync(jp.out[b] + 24 * N, 4 * W, d.G, 4 * P, 4 * W, H, cudaMemcpyDeviceToDevice, s->stream));
+    CK(s, cudaMemcpy2DAsync(jp.out[b] + 28 * N, W, d.R, P, W, H, cudaMemcpyDeviceToDevice, s->stream));
   }
   CK(s, cudaEventRecord(jp.out_ready[b], s->stream));
   CK(s, cudaStreamWaitEvent(jp.s_out, jp.out_ready[b], 0));
@@ -568,7 +587,7 @@ extern "C" {
 int coral_read_channels(coral_substrate* s, uint32_t mask, void* dst, size_t dst_bytes, int on_device) {
   if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
   if (!dst) return fail(s, CORAL_E_INVALID, "dst is NULL");
-  const long long N = s->N;
+  const long long N = s->NL, NP = s->N;
   size_t need = 0;
   for (int b = 0; b < 8; ++b)
     if (mask & (1u << b)) need += (b == 7) ? (size_t)N : (size_t)N * 4;
@@ -576,12 +595,13 @@ int coral_read_channels(coral_substrate* s, uint32_t mask, void* dst, size_t dst
   const Planes& d = s->st[s->cur];
   const cudaMemcpyKind k = kind_out(on_device);
   char* o = static_cast<char*>(dst);
-  const void* src[8] = {d.E, d.I, d.C, d.C + N, d.C + 2 * N, d.C + 3 * N, d.G, d.R};
+  const void* src[8] = {d.E, d.I, d.C, d.C + NP, d.C + 2 * NP, d.C + 3 * NP, d.G, d.R};
+  const size_t W = (size_t)s->W, H = (size_t)s->H, P = (size_t)s->P;
   for (int b = 0; b < 8; ++b) {
     if (!(mask & (1u << b))) continue;
-    const size_t bytes = (b == 7) ? (size_t)N : (size_t)N * 4;
-    CK(s, cudaMemcpyAsync(o, src[b], bytes, k, s->stream));
-    o += bytes;
+    const size_t es = (b == 7) ? 1 : 4;             // pitched rows on the device, packed rows out
+    CK(s, cudaMemcpy2DAsync(o, es * W, src[b], es * P, es * W, H, k, s->stream));
+    o += es * (size_t)N;
   }
   return check_status(s);
 }
@@ -599,14 +619,18 @@ int coral_read_stats(coral_substrate* s, int64_t step_from, int32_t n, coral_sta
 
 int coral_read_perm(coral_substrate* s, int32_t* dst_counts, int32_t* dst_perm) {
   if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
-  const long long N = s->N;
+  const long long N = s->NL;
   const int nblk = bucket_blocks(N);
   if (!s->sort_buf) {
-    const size_t words = 5 * (size_t)N + 256 * (size_t)nblk + (size_t)s->cap + 256 + 64;
+    const size_t words = 6 * (size_t)N + 256 * (size_t)nblk + (size_t)s->cap + 256 + 64;
     CK(s, dalloc(s, &s->sort_buf, words));
   }
+  // the torus cells' G packed (cell id y * W + x), then sorted
+  int32_t* keys = s->sort_buf + 5 * (size_t)N + 256 * (size_t)nblk + (size_t)s->cap + 256;
+  CK(s, cudaMemcpy2DAsync(keys, 4 * (size_t)s->W, s->st[s->cur].G, 4 * (size_t)s->P, 4 * (size_t)s->W, (size_t)s->H,
+                          cudaMemcpyDeviceToDevice, s->stream));
   SortArgs a = {};
-  a.keys_in = s->st[s->cur].G;
+  a.keys_in = keys;
   a.N = N;
   a.capacity = s->cap;
   a.k0 = s->sort_buf;
@@ -779,15 +803,15 @@ int coral_copy_rows(coral_substrate* dst, int32_t dst_row, coral_substrate* src,
   if (e == cudaSuccess) e = cudaStreamWaitEvent(dst->stream, ev, 0);
   const Planes& d = dst->st[dst->cur];
   const Planes& q = src->st[src->cur];
-  const size_t W = (size_t)dst->W, rows = (size_t)n_rows;
+  const size_t P = (size_t)dst->P, rows = (size_t)n_rows;   // whole pitched rows, padding included
   for (int p = 0; p < 6 && e == cudaSuccess; ++p)
-    e = cudaMemcpyAsync(d.E + (size_t)p * dst->N + dst_row * W, q.E + (size_t)p * src->N + src_row * W,
-                        sizeof(float) * rows * W, cudaMemcpyDeviceToDevice, dst->stream);
+    e = cudaMemcpyAsync(d.E + (size_t)p * dst->N + dst_row * P, q.E + (size_t)p * src->N + src_row * P,
+                        sizeof(float) * rows * P, cudaMemcpyDeviceToDevice, dst->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d.G + dst_row * W, q.G + src_row * W, sizeof(int32_t) * rows * W, cudaMemcpyDeviceToDevice,
+    e = cudaMemcpyAsync(d.G + dst_row * P, q.G + src_row * P, sizeof(int32_t) * rows * P, cudaMemcpyDeviceToDevice,
                         dst->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d.R + dst_row * W, q.R + src_row * W, rows * W, cudaMemcpyDeviceToDevice, dst->stream);
+    e = cudaMemcpyAsync(d.R + dst_row * P, q.R + src_row * P, rows * P, cudaMemcpyDeviceToDevice, dst->stream);
   if (e == cudaSuccess && src->stream != dst->stream) {
     e = cudaEventRecord(ev, dst->stream);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(src->stream, ev, 0);
@@ -800,8 +824,9 @@ int coral_copy_rows(coral_substrate* dst, int32_t dst_row, coral_substrate* src,
 int coral_slab_totals(coral_substrate* s, double* out) {
   if (!s || !out) return fail(s, CORAL_E_INVALID, "NULL argument");
   if (!s->totals_buf) CK(s, dalloc(s, &s->totals_buf, 6 + 6 * 256));
-  const long long j0 = s->slab ? (long long)s->row_lo * s->W : 0;
-  const long long n = s->slab ? (long long)(s->row_hi - s->row_lo) * s->W : s->N;
+  // whole pitched rows: the padding's floats are 0
+  const long long j0 = s->slab ? (long long)s->row_lo * s->P : 0;
+  const long long n = s->slab ? (long long)(s->row_hi - s->row_lo) * s->P : s->N;
   CK(s, launch_row_totals(s->st[s->cur].E, s->N, j0, n, s->totals_buf, s->stream));
   CK(s, cudaMemcpyAsync(out, s->totals_buf, 6 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   return check_status(s);

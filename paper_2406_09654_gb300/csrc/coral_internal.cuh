@@ -82,9 +82,15 @@ struct Partial {   // per-block partial sums of one step (FP64), fixed-order com
   long long c[2];  // explore, takeover
 };
 
+// Planes are pitched: row y starts at cell y * P, P = W rounded up to a multiple of 4 (rows of
+// 16-byte aligned floats for TMA and vector loads); the P - W padding cells of a row are never
+// part of the torus (G = -1, R = 0, floats 0). N = H * P is the plane length.
+__host__ __device__ inline int row_pitch(int W) { return (W + 3) & ~3; }
+
 struct __align__(8) StepArgs {
   int W, H;
-  long long N;
+  long long N;                  // H * P
+  int P;                        // row pitch in cells
   int hidden;
   int rotation;
   float k_inv, k_liq, k_exp, k_flow;
@@ -196,7 +202,7 @@ cudaError_t launch_pass1_fp32(const StepArgs& a, cudaStream_t st, int grid);
 // (box 40 x 6 x 6), or NULL when the grid does not allow it (then cp.async copies the halos).
 cudaError_t launch_pass1_bf16(const StepArgs& a, const CUtensorMap* tmap, cudaStream_t st, int grid);
 // Encodes that descriptor for planes starting at E (returns false when TMA cannot be used).
-bool encode_sensor_tmap(CUtensorMap* map, const float* E, int W, int H);
+bool encode_sensor_tmap(CUtensorMap* map, const float* E, int W, int H, int P);
 cudaError_t launch_pass2(const StepArgs& a, cudaStream_t st, int grid);
 cudaError_t launch_stats(const StepArgs& a, int n_part1, int n_part2, long long t,
                          coral_stats* ring, cudaStream_t st);
@@ -240,16 +246,19 @@ cudaError_t launch_read_dense(const GenomeArgs& g, int slot, float* dst, cudaStr
 // ctr [n][4], key [n][2], out [n][4] device arrays (16- and 8-byte aligned)
 cudaError_t launch_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out, int n, cudaStream_t st);
 cudaError_t launch_genome_distances(const float* genes, const int32_t* slots, int n, float* out, cudaStream_t st);
-cudaError_t launch_validate_state(const int32_t* G, const uint8_t* R, long long N, int cap,
+// G and R of the W x H torus in planes of pitch P (padding cells not checked)
+cudaError_t launch_validate_state(const int32_t* G, const uint8_t* R, int W, int H, int P, int cap,
                                   int* status, cudaStream_t st);
 
 struct RadiationArgs {
   int W, H;
-  long long N;
+  long long N;                // H * P
+  int P;                      // row pitch in cells
   int32_t* G;                 // current state's G (rewritten in place for the children)
-  // the cells radiation acts on: [j0, j0 + n_own) of G, whose global cell ids (the Philox
-  // counter and the hit order) start at gid0; the whole grid (0, N, 0) unless the substrate is
-  // one row slab of a larger world
+  // the cells radiation acts on: the whole rows [j0, j0 + n_own) of G (pitched indices, j0 a
+  // multiple of P; padding cells skipped), whose global cell ids (y * W + x: the Philox counter
+  // and the hit order) start at gid0; the whole grid (0, N, 0) unless the substrate is one row
+  // slab of a larger world
   long long j0, n_own, gid0;
   GenomeArgs g;
   uint32_t thr_mut, thr_merge;

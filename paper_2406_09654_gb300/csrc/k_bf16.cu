@@ -115,7 +115,7 @@ __device__ __forceinline__ void issue_halo(const StepArgs& a, int x0, int y0, ui
     const int sgm = warp + k * (kThreads / 32);
     const int ch = sgm / kHaloH, hy = sgm - ch * kHaloH;
     const int gy = wraps ? fold(y0 - 1 + hy, a.H, small_h) : y0 - 1 + hy;
-    const long long off = (long long)ch * a.N + (long long)gy * a.W;
+    const long long off = (long long)ch * a.N + (long long)gy * a.P;
     const float* row = a.cur.E + off;
     const uint32_t d = dst + 4u * (uint32_t)(ch * kStageCh + hy * kStageW + 3);
     if (lane < kHaloW) tc::cp_async4(d + 4u * lane, row + col_a);
@@ -222,7 +222,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     r_next = 0;
     const int gx = x0 + lx, gy = y0 + ly;
     if (gx < W && gy < Hh) {
-      const int jn = gy * W + gx;
+      const int jn = gy * a.P + gx;
       g_next = __ldg(a.cur.G + jn);
       r_next = a.rotation ? (int)__ldg(a.cur.R + jn) : 0;
     }
@@ -261,7 +261,7 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
     }
     const int gx = x0 + lx, gy = y0 + ly;
     const bool valid = gx < W && gy < Hh;
-    const long long j = (long long)gy * W + gx;
+    const long long j = (long long)gy * a.P + gx;
     const int g = g_next, r = r_next;
     // this tile's halo: every thread waits on the TMA barrier itself; a cp.async tile needs
     // the CTA barrier to see the other threads' copies
@@ -692,9 +692,9 @@ cudaError_t launch_pass1_bf16(const StepArgs& a, const CUtensorMap* tmap, cudaSt
   return cudaGetLastError();
 }
 
-bool encode_sensor_tmap(CUtensorMap* map, const float* E, int W, int H) {
-  // rows must be a multiple of 16 bytes and hold the 40-wide box; planes of 6 rows at least
-  if ((W & 3) != 0 || W < kStageW || H < kHaloH) return false;
+bool encode_sensor_tmap(CUtensorMap* map, const float* E, int W, int H, int P) {
+  // rows (pitch P) must be a multiple of 16 bytes; the torus must hold the 40-wide box and 6 rows
+  if ((P & 3) != 0 || W < kStageW || H < kHaloH) return false;
   if ((reinterpret_cast<uintptr_t>(E) & 15) != 0) return false;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
@@ -708,7 +708,7 @@ bool encode_sensor_tmap(CUtensorMap* map, const float* E, int W, int H) {
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, 6};
-  const cuuint64_t strides[2] = {(cuuint64_t)W * 4, (cuuint64_t)W * (cuuint64_t)H * 4};
+  const cuuint64_t strides[2] = {(cuuint64_t)P * 4, (cuuint64_t)P * (cuuint64_t)H * 4};
   const cuuint32_t box[3] = {(cuuint32_t)kStageW, (cuuint32_t)kHaloH, 6};
   const cuuint32_t estr[3] = {1, 1, 1};
   return encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(E), dims, strides, box, estr,

@@ -143,9 +143,10 @@ __global__ void __launch_bounds__(256) k_bf16_pack(GenomeArgs g, const int32_t* 
   }
 }
 
-__global__ void k_validate(const int32_t* G, const uint8_t* R, long long N, int cap, int* status) {
+__global__ void k_validate(const int32_t* G, const uint8_t* R, int W, long long N, int P, int cap, int* status) {
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < N;
        j += (long long)gridDim.x * blockDim.x) {
+    if ((int)(j % P) >= W) continue;                  // row padding
     if ((G && (G[j] < 0 || G[j] >= cap)) || (R && R[j] > 3)) atomicCAS(status, 0, (int)CORAL_E_INVALID);
   }
 }
@@ -164,19 +165,26 @@ struct Hit {
   uint32_t bits;
 };
 
+// Global cell id (y * W + x over the world) of pitched cell j of the own rows.
+__device__ __forceinline__ long long global_id(const RadiationArgs& r, long long j) {
+  const long long l = j - r.j0;
+  return r.gid0 + (l / r.P) * r.W + l % r.P;
+}
+
 __device__ __forceinline__ Hit radiation_hit(const RadiationArgs& r, long long j) {
   Hit h = {false, false, false, 0, -1, 0};
-  const uint32_t cell = (uint32_t)(j - r.j0 + r.gid0);       // global cell id
+  if ((int)(j % r.P) >= r.W) return h;                // row padding
+  const uint32_t cell = (uint32_t)global_id(r, j);
   const uint32_t cap = (uint32_t)r.g.capacity;
   if ((uint32_t)r.G[j] >= cap) return h;              // invalid GenomeIndex: never a parent
   if (r.thr_mut) h.mut = draw(cell, r.step, 0, 0, r.world, r.seed).x < r.thr_mut;
   if (r.thr_merge) {
     const uint4 w = draw(cell, r.step, 1, 0, r.world, r.seed);
     if (w.x < r.thr_merge) {
-      const int x = (int)(j % r.W), y = (int)(j / r.W);
+      const int x = (int)(j % r.P), y = (int)(j / r.P);
       int dx, dy;
       octant_offset(2 * (int)(w.y & 3u), dx, dy);     // von Neumann N, E, S, W
-      const long long n = (long long)wrap(y + dy, r.H) * r.W + wrap(x + dx, r.W);
+      const long long n = (long long)wrap(y + dy, r.H) * r.P + wrap(x + dx, r.W);
       const int32_t gp = r.G[n];
       if (gp != r.G[j] && (uint32_t)gp < cap) {
         h.merge = true;
@@ -284,7 +292,7 @@ __global__ void __launch_bounds__(kRadThreads) k_rad_emit(RadiationArgs r) {
     mask &= mask - 1;
     const Hit h = radiation_hit(r, base + i);
     if (pos < r.max_hits) {
-      r.hits[pos] = make_int4((int)(base + i - r.j0 + r.gid0), h.g, h.merge ? h.gp : -1, (h.mut ? 1 : 0) | (h.merge ? 2 : 0));
+      r.hits[pos] = make_int4((int)global_id(r, base + i), h.g, h.merge ? h.gp : -1, (h.mut ? 1 : 0) | (h.merge ? 2 : 0));
       r.hitbits[pos] = h.bits;
     }
     ++pos;
@@ -424,8 +432,8 @@ __global__ void __launch_bounds__(128) k_rad_assign(RadiationArgs r) {
 #pragma unroll
     for (int k = 0; k < kGenes; ++k) dst[k] = c[k];
     r.g.parent[slot] = h.y;
-    const long long lj = (long long)h.x - r.gid0 + r.j0;     // the hit cell in this grid, if own
-    if (lj >= r.j0 && lj < r.j0 + r.n_own) r.G[lj] = slot;
+    const long long l = (long long)h.x - r.gid0;             // the hit cell in this grid, if own
+    if (l >= 0 && l < r.n_own / r.P * r.W) r.G[r.j0 + (l / r.W) * r.P + l % r.W] = slot;
     r.newslots[i] = slot;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -695,9 +703,9 @@ cudaError_t launch_read_dense(const GenomeArgs& g, int slot, float* dst, cudaStr
   return cudaGetLastError();
 }
 
-cudaError_t launch_validate_state(const int32_t* G, const uint8_t* R, long long N, int cap, int* status,
+cudaError_t launch_validate_state(const int32_t* G, const uint8_t* R, int W, int H, int P, int cap, int* status,
                                   cudaStream_t st) {
-  k_validate<<<1024, 256, 0, st>>>(G, R, N, cap, status);
+  k_validate<<<1024, 256, 0, st>>>(G, R, W, (long long)H * P, P, cap, status);
   return cudaGetLastError();
 }
 

@@ -49,20 +49,19 @@ __device__ void block_partial(const double (&s)[NS], const long long (&c)[NC], P
 // One thread per cell: gather the rotation-ordered 3x3 neighbourhood of the six sensor
 // channels straight from the SoA planes, run the FP32 net with FMA, apply the actuators.
 __global__ void __launch_bounds__(kP1Threads) k_pass1_fp32(const StepArgs a) {
-  const int W = a.W, H = a.H;
+  const int W = a.W, H = a.H, P = a.P;
   const long long N = a.N;
   double accC[4] = {0, 0, 0, 0};
   long long accX[1] = {0};
   const long long stride = (long long)gridDim.x * kP1Threads;
   for (long long base = (long long)blockIdx.x * kP1Threads; base < N; base += stride) {
     const long long j = base + threadIdx.x;
-    const bool valid = j < N;
+    const int y = (int)(j / P), x = (int)(j - (long long)y * P);
+    const bool valid = j < N && x < W;               // row padding is not part of the torus
     CellOut o;
     o.C[0] = o.C[1] = o.C[2] = o.C[3] = 0.0f;
     o.xdir = kNoExplore;
     if (valid) {
-      const int jj = (int)j;
-      const int y = jj / W, x = jj - y * W;
       const int r = a.rotation ? (int)a.cur.R[j] : 0;
       float in[kIn];
       load6(a.cur, j, N, in);
@@ -70,7 +69,7 @@ __global__ void __launch_bounds__(kP1Threads) k_pass1_fp32(const StepArgs a) {
       for (int p = 1; p < 9; ++p) {
         int dx, dy;
         octant_offset((2 * r + rank_delta(p)) & 7, dx, dy);
-        const long long n = (long long)wrap(y + dy, H) * W + wrap(x + dx, W);
+        const long long n = (long long)wrap(y + dy, H) * P + wrap(x + dx, W);
         load6(a.cur, n, N, in + 6 * p);
       }
       const int gj = a.cur.G[j];
@@ -158,171 +157,13 @@ __device__ __forceinline__ bool is_day_now(const StepArgs& a) {
   return (t % a.day_period) * 2 < a.day_period;
 }
 
-// Pass 2: exploration resolve and takeover, energy flow, day/night, for any row width. Each
-// thread resolves 4 consecutive cells of the flattened grid (they may continue on the next
-// row): 16-byte loads and stores of the cells' own planes, the east / west neighbour's data
-// from the chunk where that neighbour is in it; CTA `cta` of `ncta` strides over the chunks,
-// partial sums to a.part2[cta]. Same per-cell arithmetic and order as pass2_x4_body.
-__device__ __forceinline__ void pass2_c4_body(const StepArgs& a, const int cta, const int ncta) {
-  const int W = a.W, H = a.H;
-  const int N = (int)a.N;
-  const int n_chunks = (N + 3) >> 2;
-  const bool day = is_day_now(a);
-  // the I plane starts N floats after the E plane: 16-byte aligned only when N % 4 == 0
-  const bool i_vec = (N & 3) == 0;
-  double acc[2] = {0, 0};
-  long long accT[1] = {0};
-  const int stride = ncta * kP2Threads;
-  for (int base = cta * kP2Threads; base < n_chunks; base += stride) {
-    const int c = base + threadIdx.x;
-    float e_sum = 0.0f, i_sum = 0.0f;
-    int takes = 0;
-    if (c < n_chunks) {
-      const int j = c << 2;
-      const int len = N - j < 4 ? N - j : 4;
-      const int y0 = j / W, x0 = j - y0 * W;
-      int xs[4], ys[4];
-      {
-        int x = x0, y = y0;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          xs[k] = x;
-          ys[k] = y;
-          if (++x == W) {
-            x = 0;
-            ++y;
-          }
-        }
-      }
-      float4 rc[4];                                             // keep, I1, q, xamt
-      float vIt[4];
-      int vG[4];
-      uint32_t vR[4], vd[4];
-      if (len == 4) {
-        const float4 It = i_vec ? *reinterpret_cast<const float4*>(a.cur.I + j)
-                                : make_float4(a.cur.I[j], a.cur.I[j + 1], a.cur.I[j + 2], a.cur.I[j + 3]);
-        const int4 Gc = *reinterpret_cast<const int4*>(a.cur.G + j);
-        const uint32_t Rc = *reinterpret_cast<const uint32_t*>(a.cur.R + j);
-        const uint32_t dc = *reinterpret_cast<const uint32_t*>(a.p1.xdir + j);
-        vIt[0] = It.x; vIt[1] = It.y; vIt[2] = It.z; vIt[3] = It.w;
-        vG[0] = Gc.x; vG[1] = Gc.y; vG[2] = Gc.z; vG[3] = Gc.w;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          vR[k] = (Rc >> (8 * k)) & 0xFFu;
-          vd[k] = (dc >> (8 * k)) & 0xFFu;
-          rc[k] = a.p1.rec[j + k];
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          const bool in = k < len;
-          vIt[k] = in ? a.cur.I[j + k] : 0.0f;
-          vG[k] = in ? a.cur.G[j + k] : 0;
-          vR[k] = in ? a.cur.R[j + k] : 0u;
-          vd[k] = in ? a.p1.xdir[j + k] : (uint32_t)kNoExplore;
-          rc[k] = in ? a.p1.rec[j + k] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-      }
-      float oE[4], oI[4];
-      int oG[4];
-      uint32_t oR[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        oE[k] = oI[k] = 0.0f;
-        oG[k] = 0;
-        oR[k] = 0;
-        if (k >= len) continue;
-        const int x = xs[k], y = ys[k];
-        const int row = y * W;
-        const int nN = (y == 0 ? H - 1 : y - 1) * W + x, nS = (y == H - 1 ? 0 : y + 1) * W + x;
-        const bool e_in = k + 1 < len && x + 1 < W, w_in = k > 0 && x > 0;   // neighbour in the chunk
-        const int nE = e_in ? j + k + 1 : row + (x + 1 == W ? 0 : x + 1);
-        const int nW = w_in ? j + k - 1 : row + (x == 0 ? W - 1 : x - 1);
-        const float2 fN = *reinterpret_cast<const float2*>(&a.p1.rec[nN].z);   // q, xamt
-        const float2 fS = *reinterpret_cast<const float2*>(&a.p1.rec[nS].z);
-        float2 fE, fW;
-        uint32_t dE, dW;
-        if (e_in) {
-          fE = make_float2(rc[k + 1].z, rc[k + 1].w);
-          dE = vd[k + 1];
-        } else {
-          fE = *reinterpret_cast<const float2*>(&a.p1.rec[nE].z);
-          dE = a.p1.xdir[nE];
-        }
-        if (w_in) {
-          fW = make_float2(rc[k - 1].z, rc[k - 1].w);
-          dW = vd[k - 1];
-        } else {
-          fW = *reinterpret_cast<const float2*>(&a.p1.rec[nW].z);
-          dW = a.p1.xdir[nW];
-        }
-        // neighbours in N, E, S, W order: direction byte, amount, flow quotient
-        const uint32_t nd[4] = {a.p1.xdir[nN], dE, a.p1.xdir[nS], dW};
-        const float na[4] = {fN.y, fE.y, fS.y, fW.y};
-        const float nq[4] = {fN.x, fE.x, fS.x, fW.x};
-        const int nbi[4] = {nN, nE, nS, nW};
-        const float I1 = rc[k].y;
-        float I2 = I1 - rc[k].w;
-        float best = -INFINITY;
-        int bd = -1;
-#pragma unroll
-        for (int D = 0; D < 4; ++D) {
-          if (nd[D] == (uint32_t)((D + 2) & 3)) {
-            I2 += na[D];
-            if (na[D] > best) { best = na[D]; bd = D; }       // strict: N, E, S, W keep ties
-          }
-        }
-        const bool take = bd >= 0 && best > I1;
-        int g = vG[k];
-        uint32_t r = vR[k];
-        if (take) {
-          const int nb = bd == 0 ? nbi[0] : (bd == 1 ? nbi[1] : (bd == 2 ? nbi[2] : nbi[3]));
-          g = a.cur.G[nb];
-          r = bd == 0 ? nd[0] : (bd == 1 ? nd[1] : (bd == 2 ? nd[2] : nd[3]));
-          ++takes;
-        }
-        const float inflow = ((nq[0] + nq[1]) + nq[2]) + nq[3];
-        const float E2 = rc[k].x + vIt[k] * inflow;
-        oE[k] = day ? E2 + a.e_day : E2 - a.e_night * E2;
-        oI[k] = I2;
-        oG[k] = g;
-        oR[k] = r;
-        e_sum += oE[k];
-        i_sum += oI[k];
-      }
-      if (len == 4) {
-        *reinterpret_cast<float4*>(a.nxt.E + j) = make_float4(oE[0], oE[1], oE[2], oE[3]);
-        if (i_vec) {
-          *reinterpret_cast<float4*>(a.nxt.I + j) = make_float4(oI[0], oI[1], oI[2], oI[3]);
-        } else {
-#pragma unroll
-          for (int k = 0; k < 4; ++k) a.nxt.I[j + k] = oI[k];
-        }
-        *reinterpret_cast<int4*>(a.nxt.G + j) = make_int4(oG[0], oG[1], oG[2], oG[3]);
-        *reinterpret_cast<uint32_t*>(a.nxt.R + j) = oR[0] | (oR[1] << 8) | (oR[2] << 16) | (oR[3] << 24);
-      } else {
-        for (int k = 0; k < len; ++k) {
-          a.nxt.E[j + k] = oE[k];
-          a.nxt.I[j + k] = oI[k];
-          a.nxt.G[j + k] = oG[k];
-          a.nxt.R[j + k] = (uint8_t)oR[k];
-        }
-      }
-    }
-    warp_accumulate(e_sum, acc[0]);
-    warp_accumulate(i_sum, acc[1]);
-    const int tk = warp_sum_i(takes);
-    if ((threadIdx.x & 31) == 0) accT[0] += tk;
-  }
-  block_partial<2, 1>(acc, accT, a.part2, 0, 1, cta);
-}
-
-// Pass 2 for rows that are a multiple of 4 cells wide: each thread resolves 4 consecutive cells
-// of one row with 16-byte loads of the pass-1 buffers (same per-cell arithmetic and order as
-// pass2_c4_body).
-__device__ __forceinline__ void pass2_x4_body(const StepArgs& a, const int cta, const int ncta) {
-  const int W = a.W, H = a.H;
-  const int cpr = W >> 2;                       // chunks per row
+// Pass 2: exploration resolve and takeover, energy flow, day/night. Each thread resolves 4
+// consecutive cells of one pitched row (16-byte loads and stores; the last chunk of a row holds
+// the row's padding when the width is not a multiple of 4: its padding cells keep G = -1, R = 0
+// and get E = I = 0). CTA `cta` of `ncta` strides over the chunks, partial sums to a.part2[cta].
+__device__ __forceinline__ void pass2_body(const StepArgs& a, const int cta, const int ncta) {
+  const int W = a.W, H = a.H, P = a.P;
+  const int cpr = P >> 2;                       // chunks per row
   const int n_chunks = cpr * H;
   const bool day = is_day_now(a);
   double acc[2] = {0, 0};
@@ -336,17 +177,19 @@ __device__ __forceinline__ void pass2_x4_body(const StepArgs& a, const int cta, 
     if (valid) {
       const int y = c / cpr;
       const int x = (c - y * cpr) << 2;
-      const int j = y * W + x;
-      const int jn = (y == 0 ? H - 1 : y - 1) * W + x;          // same columns, row above
-      const int js = (y == H - 1 ? 0 : y + 1) * W + x;          // row below
-      const int jw = y * W + (x == 0 ? W - 1 : x - 1);          // left of the first cell
-      const int je = y * W + (x + 4 == W ? 0 : x + 4);          // right of the last cell
-      float4 rc[4], rn[4], rs[4];                               // keep, I1, q, xamt
+      const int nv = min(4, W - x);                             // torus cells of this chunk
+      const int j = y * P + x;
+      const int jn = (y == 0 ? H - 1 : y - 1) * P + x;          // same columns, row above
+      const int js = (y == H - 1 ? 0 : y + 1) * P + x;          // row below
+      const int jw = y * P + (x == 0 ? W - 1 : x - 1);          // west of the first cell
+      const int je = y * P + (x + 4 >= W ? 0 : x + 4);          // east of the last torus cell
+      float4 rc[4];                                             // keep, I1, q, xamt
+      float2 rn[4], rs[4];                                      // the rows above and below: q, xamt
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         rc[k] = a.p1.rec[j + k];
-        rn[k] = a.p1.rec[jn + k];
-        rs[k] = a.p1.rec[js + k];
+        rn[k] = *reinterpret_cast<const float2*>(&a.p1.rec[jn + k].z);
+        rs[k] = *reinterpret_cast<const float2*>(&a.p1.rec[js + k].z);
       }
       const float4 It = *reinterpret_cast<const float4*>(a.cur.I + j);
       const uint32_t dc = *reinterpret_cast<const uint32_t*>(a.p1.xdir + j);
@@ -362,7 +205,7 @@ __device__ __forceinline__ void pass2_x4_body(const StepArgs& a, const int cta, 
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         vkp[k] = rc[k].x; vI1[k] = rc[k].y; vq[k] = rc[k].z; vxa[k] = rc[k].w;
-        vqN[k] = rn[k].z; vxaN[k] = rn[k].w; vqS[k] = rs[k].z; vxaS[k] = rs[k].w;
+        vqN[k] = rn[k].x; vxaN[k] = rn[k].y; vqS[k] = rs[k].x; vxaS[k] = rs[k].y;
       }
       const float vIt[4] = {It.x, It.y, It.z, It.w};
       const int vG[4] = {Gc.x, Gc.y, Gc.z, Gc.w};
@@ -371,13 +214,21 @@ __device__ __forceinline__ void pass2_x4_body(const StepArgs& a, const int cta, 
       uint32_t oR = 0;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
+        if (k >= nv) {                                          // row padding keeps its values
+          oE[k] = 0.0f;
+          oI[k] = 0.0f;
+          oG[k] = vG[k];
+          oR |= ((Rc >> (8 * k)) & 0xFFu) << (8 * k);
+          continue;
+        }
+        const bool last = k == nv - 1;                          // its east neighbour is past the chunk
         // neighbours of cell x+k in N, E, S, W order: direction byte, amount, flow quotient
         const uint32_t nd[4] = {(dN >> (8 * k)) & 0xFFu,
-                                k < 3 ? (dc >> (8 * (k + 1))) & 0xFFu : (uint32_t)dE,
+                                !last ? (dc >> (8 * (k + 1))) & 0xFFu : (uint32_t)dE,
                                 (dS >> (8 * k)) & 0xFFu,
                                 k > 0 ? (dc >> (8 * (k - 1))) & 0xFFu : (uint32_t)dW};
-        const float na[4] = {vxaN[k], k < 3 ? vxa[k + 1] : xaE, vxaS[k], k > 0 ? vxa[k - 1] : xaW};
-        const float nq[4] = {vqN[k], k < 3 ? vq[k + 1] : qE, vqS[k], k > 0 ? vq[k - 1] : qW};
+        const float na[4] = {vxaN[k], !last ? vxa[k < 3 ? k + 1 : 3] : xaE, vxaS[k], k > 0 ? vxa[k - 1] : xaW};
+        const float nq[4] = {vqN[k], !last ? vq[k < 3 ? k + 1 : 3] : qE, vqS[k], k > 0 ? vq[k - 1] : qW};
         float I2 = vI1[k] - vxa[k];
         float best = -INFINITY;
         int bd = -1;
@@ -392,7 +243,7 @@ __device__ __forceinline__ void pass2_x4_body(const StepArgs& a, const int cta, 
         int g = vG[k];
         uint32_t r = (Rc >> (8 * k)) & 0xFFu;
         if (take) {
-          const int nb = bd == 0 ? jn + k : (bd == 2 ? js + k : (bd == 1 ? (k < 3 ? j + k + 1 : je) : (k > 0 ? j + k - 1 : jw)));
+          const int nb = bd == 0 ? jn + k : (bd == 2 ? js + k : (bd == 1 ? (!last ? j + k + 1 : je) : (k > 0 ? j + k - 1 : jw)));
           g = a.cur.G[nb];
           r = bd == 0 ? nd[0] : (bd == 1 ? nd[1] : (bd == 2 ? nd[2] : nd[3]));
           ++takes;
@@ -419,12 +270,8 @@ __device__ __forceinline__ void pass2_x4_body(const StepArgs& a, const int cta, 
   block_partial<2, 1>(acc, accT, a.part2, 0, 1, cta);
 }
 
-__global__ void __launch_bounds__(kP2Threads) k_pass2_c4(const __grid_constant__ StepArgs a) {
-  pass2_c4_body(a, blockIdx.x, gridDim.x);
-}
-
 __global__ void __launch_bounds__(kP2Threads) k_pass2_x4(const __grid_constant__ StepArgs a) {
-  pass2_x4_body(a, blockIdx.x, gridDim.x);
+  pass2_body(a, blockIdx.x, gridDim.x);
 }
 
 __global__ void __launch_bounds__(kP2Threads) k_pass2_batch(const __grid_constant__ BatchTable bt, const int parity) {
@@ -432,11 +279,7 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2_batch(const __grid_constan
   const int w = bt.cta_world2[blockIdx.x];
   copy_args_to_shared(&a, &bt.args[parity * bt.n + w]);
   __syncthreads();
-  const int cta = blockIdx.x - bt.world_first2[w], ncta = bt.world_ctas2[w];
-  if ((a.W & 3) == 0 && a.W >= 8)
-    pass2_x4_body(a, cta, ncta);
-  else
-    pass2_c4_body(a, cta, ncta);
+  pass2_body(a, blockIdx.x - bt.world_first2[w], bt.world_ctas2[w]);
 }
 
 // Fixed-order FP64 combination of the block partials into the stats ring.
@@ -540,11 +383,7 @@ int occupancy_grid(const void* fn, int threads, size_t smem, int sms) {
 }  // namespace
 
 int pass1_fp32_grid(int sms) { return occupancy_grid((const void*)k_pass1_fp32, kP1Threads, 0, sms); }
-int pass2_grid(int sms) {
-  const int a = occupancy_grid((const void*)k_pass2_c4, kP2Threads, 0, sms);
-  const int b = occupancy_grid((const void*)k_pass2_x4, kP2Threads, 0, sms);
-  return a < b ? a : b;
-}
+int pass2_grid(int sms) { return occupancy_grid((const void*)k_pass2_x4, kP2Threads, 0, sms); }
 
 cudaError_t launch_pass1_fp32(const StepArgs& a, cudaStream_t st, int grid) {
   k_pass1_fp32<<<grid, kP1Threads, 0, st>>>(a);
@@ -552,10 +391,7 @@ cudaError_t launch_pass1_fp32(const StepArgs& a, cudaStream_t st, int grid) {
 }
 
 cudaError_t launch_pass2(const StepArgs& a, cudaStream_t st, int grid) {
-  if ((a.W & 3) == 0 && a.W >= 8)
-    k_pass2_x4<<<grid, kP2Threads, 0, st>>>(a);
-  else
-    k_pass2_c4<<<grid, kP2Threads, 0, st>>>(a);
+  k_pass2_x4<<<grid, kP2Threads, 0, st>>>(a);
   return cudaGetLastError();
 }
 
