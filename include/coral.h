@@ -240,7 +240,10 @@ int coral_launch_config(const coral_substrate* s, int32_t* grid_pass1, int32_t* 
 /*
  * Batched stepping of many independent worlds (many substrates in one launch per pass, the
  * per-step launch sequence replayed as a CUDA graph). All worlds: BF16 path, the same hidden
- * size, radiation off, a genome table loaded, the current CUDA device. The CTAs of each launch
+ * size, a genome table loaded (CPPN genes where radiation is on), whole worlds (no row slabs),
+ * the current CUDA device. Each world keeps its own radiation schedule: after a step that ends
+ * one of its epochs, its radiation (Section "System Design", Fig. 1 C) runs on the batch stream
+ * before the next step's graph, as coral_step runs it. The CTAs of each launch
  * are divided among the worlds in proportion to their sizes, at least one each (each CTA works
  * on one world; a launch asks for 32 times the CTAs of its launch shape, so that the block
  * scheduler evens out small and large worlds), and a world's cells are bit-identical to
@@ -248,8 +251,8 @@ int coral_launch_config(const coral_substrate* s, int32_t* grid_pass1, int32_t* 
  * each coral_batch_step it waits for work already enqueued on the worlds' streams, and the
  * worlds' streams wait for the batch's steps, so per-world calls (reads, loads) stay ordered.
  * The substrates stay owned by the caller and must outlive the batch.
- * Errors: E_INVALID (mixed hidden sizes / paths / devices, radiation on), E_STATE (no genome
- * table), E_OOM, E_CUDA.
+ * Errors: E_INVALID (mixed hidden sizes / paths / devices, a row slab), E_STATE (no genome
+ * table, radiation with direct nets), E_OOM, E_CUDA.
  */
 typedef struct coral_batch coral_batch;
 int coral_batch_create(coral_substrate* const* worlds, int32_t n, coral_batch** out);
@@ -259,7 +262,8 @@ int coral_batch_step(coral_batch* b, int32_t n_steps);
 /* Same, with a CUDA event pair around every step: step_ms[n_steps] (host). Synchronises. */
 int coral_batch_step_timed(coral_batch* b, int32_t n_steps, float* step_ms);
 /*
- * Autotuner: times trial_steps steps (after one warm-up) for each candidate launch shape —
+ * Autotuner: times trial_steps steps (after one warm-up; graphs only, no radiation, so that
+ * the genome tables stay as they are) for each candidate launch shape —
  * pass-1 CTAs per SM in {3, 4, 5, 6} x pass-2 CTAs per SM in {1, 2, 3}, each times 32 as
  * above — keeps the fastest and
  * restores every world's state, step index and stats ring afterwards (also after an error,

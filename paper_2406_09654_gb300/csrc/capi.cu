@@ -1124,7 +1124,11 @@ extern "C" int coral_batch_create(coral_substrate* const* worlds, int32_t n, cor
       if (!s) { rc = bfail(b, CORAL_E_INVALID, "NULL world"); break; }
       if (s->p.path != CORAL_NET_BF16_GROUPED) { rc = bfail(b, CORAL_E_INVALID, "batched worlds use the BF16 path"); break; }
       if (s->p.hidden != worlds[0]->p.hidden) { rc = bfail(b, CORAL_E_INVALID, "batched worlds share one hidden size"); break; }
-      if (s->p.radiation_every > 0) { rc = bfail(b, CORAL_E_INVALID, "radiation is not batched"); break; }
+      if (s->p.radiation_every > 0 && !s->has_cppn) {
+        rc = bfail(b, CORAL_E_STATE, "radiation needs CPPN genomes (direct nets cannot mutate)");
+        break;
+      }
+      if (s->slab) { rc = bfail(b, CORAL_E_INVALID, "row-slab substrates are not batched"); break; }
       if (!s->genomes_loaded) { rc = bfail(b, CORAL_E_STATE, "a world has no genome table"); break; }
       if (dev >= 0 && s->device != dev) { rc = bfail(b, CORAL_E_INVALID, "worlds on different devices"); break; }
       dev = s->device;
@@ -1183,7 +1187,9 @@ extern "C" int coral_batch_destroy(coral_batch* b) {
 }
 
 namespace {
-int batch_run(coral_batch* b, int32_t n_steps, float* step_ms) {
+// radiation = false: the graphs alone (the tuner's trial steps, which must leave the genome
+// tables as they are).
+int batch_run(coral_batch* b, int32_t n_steps, float* step_ms, bool radiation = true) {
   if (!b) return bfail(nullptr, CORAL_E_INVALID, "NULL batch");
   if (n_steps < 0) return bfail(b, CORAL_E_INVALID, "n_steps must be >= 0");
   if (n_steps == 0) return CORAL_OK;
@@ -1198,6 +1204,17 @@ int batch_run(coral_batch* b, int32_t n_steps, float* step_ms) {
   }
   for (int i = 0; i < n_steps; ++i) {
     BCK(b, cudaGraphLaunch(b->graph[i & 1], b->stream));
+    // radiation of the worlds whose step t = t0 + i ends an epoch: on the post-step state
+    // (buffer cur ^ ((i + 1) & 1)), on the batch stream before the next step's graph
+    for (coral_substrate* s : b->worlds) {
+      const long long t = s->t + i;
+      if (!radiation || s->p.radiation_every <= 0 || (t + 1) % s->p.radiation_every != 0) continue;
+      const int save = s->cur;
+      s->cur = save ^ ((i + 1) & 1);
+      const RadiationArgs r = radiation_args(s, t);
+      s->cur = save;
+      BCK(b, launch_radiation(r, b->stream));
+    }
     if (step_ms) BCK(b, cudaEventRecord(ev[i + 1], b->stream));
   }
   if ((rc = batch_leave(b, n_steps)) != CORAL_OK) return rc;
@@ -1259,7 +1276,7 @@ extern "C" int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* ch
       b->cps1 = c1s[i1];
       b->cps2 = c2s[i2];
       if ((rc = batch_configure(b)) != CORAL_OK) break;
-      if ((rc = batch_run(b, trial_steps + 1, ms.data())) != CORAL_OK) break;
+      if ((rc = batch_run(b, trial_steps + 1, ms.data(), false)) != CORAL_OK) break;
       float tot = 0;
       for (int k = 1; k <= trial_steps; ++k) tot += ms[k];
       if (tot < best) {

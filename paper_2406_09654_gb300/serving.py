@@ -62,6 +62,7 @@ class CoralBackend:
         self.coral = coral
         self.path = coral.BF16_GROUPED if path is None else path
         self.pool = ThreadPoolExecutor(max_workers=build_threads)
+        self.stepper = ThreadPoolExecutor(max_workers=1)
         self.futures = {}
 
     def prepare(self, world):
@@ -79,6 +80,11 @@ class CoralBackend:
 
     def step(self, batch, n):
         return batch.step_timed(n)       # per-step device time (ms)
+
+    def step_async(self, batch, n):
+        """The same steps on a host thread (the call waits for the device without holding the
+        interpreter), so that the server creates the next worlds meanwhile."""
+        return self.stepper.submit(batch.step_timed, n)
 
     def read(self, handle):
         return handle.read_channels()
@@ -104,28 +110,39 @@ class WorldServer:
         self.sleep = sleep
 
     def run(self, requests):
-        """Serve `requests` (arrival times in seconds from now). Returns (completed, report)."""
+        """Serve `requests` (arrival times in seconds from now). Returns (completed, report).
+
+        With a backend that steps asynchronously (``step_async``), the next requests' worlds are
+        admitted and created on the host while the current chunk of steps runs on the device;
+        they join the batch when the chunk ends."""
         pending = sorted(requests)
         waiting = []                     # arrived, not admitted (FIFO by arrival)
-        active = {}                      # rid -> [request, handle, remaining, admitted_at, bytes]
+        active = {}                      # rid -> [request, handle, remaining, admitted_at, bytes]: in the batch
+        joining = {}                     # admitted and created, joining at the next rebuild
         used = 0
         batch = None
         dirty = False
         step_lat = []                    # (batch step ms, resident worlds) per batched step
         req_step_ms = []                 # one entry per request-step: the device time of its step
-        req_step_wall = []               # one entry per request-step: wall time of its chunk / steps
+        req_step_wall = []               # one entry per request-step: wall time between chunk ends / steps
         completed = []
         work = 0
         t0 = self.clock()
         peak_used = 0
-        while pending or waiting or active:
+        inflight = None                  # (future or result, steps, resident worlds)
+        last_end = None                  # wall clock at the end of the last chunk
+        asynchronous = hasattr(self.backend, "step_async")
+        host = {"create_s": 0.0, "batch_s": 0.0, "read_free_s": 0.0, "wait_s": 0.0}
+
+        def admit():
+            nonlocal used, peak_used
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.pop(0))
             if hasattr(self.backend, "prepare"):
                 for r in waiting[:self.prefetch]:
                     self.backend.prepare(r.world)
-            # admission: arrival order, while the budget allows (a request that can never fit
+            # arrival order, while the budget and the slots allow (a request that can never fit
             # on its own is rejected rather than blocking the queue)
             while waiting:
                 r = waiting[0]
@@ -134,44 +151,70 @@ class WorldServer:
                     waiting.pop(0)
                     completed.append(Completed(r.rid, r.arrival, -1.0, -1.0, 0, r.world.n_cells, {}))
                     continue
-                if used + need > self.budget or (self.max_worlds and len(active) >= self.max_worlds):
+                resident = len(active) + len(joining)
+                if used + need > self.budget or (self.max_worlds and resident >= self.max_worlds):
                     break
                 waiting.pop(0)
-                active[r.rid] = [r, self.backend.create(r.world), r.steps, self.clock() - t0, need]
+                c0 = self.clock()
+                joining[r.rid] = [r, self.backend.create(r.world), r.steps, self.clock() - t0, need]
+                host["create_s"] += self.clock() - c0
                 used += need
                 peak_used = max(peak_used, used)
+
+        while pending or waiting or active or joining or inflight:
+            admit()
+            if inflight is not None:                          # the chunk ends
+                fut, n, resident = inflight
+                c0 = self.clock()
+                ms = fut.result() if asynchronous else fut
+                host["wait_s"] += self.clock() - c0
+                inflight = None
+                for m in ms:
+                    step_lat.append((float(m), resident))
+                    req_step_ms.extend([float(m)] * resident)
+                work += n * sum(v[0].world.n_cells for v in active.values())
+                done = [rid for rid, v in active.items() if v[2] - n <= 0]
+                for v in active.values():
+                    v[2] -= n
+                if done:
+                    c0 = self.clock()
+                    self.backend.free_batch(batch)
+                    batch = None
+                    for rid in done:
+                        r, h, _, adm, need = active.pop(rid)
+                        res = self.backend.read(h)
+                        self.backend.free(h)
+                        used -= need
+                        completed.append(Completed(rid, r.arrival, adm, self.clock() - t0, r.steps,
+                                                   r.world.n_cells, res))
+                    host["read_free_s"] += self.clock() - c0
+                end = self.clock()
+                req_step_wall.extend([1e3 * (end - last_end) / n] * (resident * n))
+                last_end = end
+                admit()                                       # freed memory and slots
+            if joining:
+                active.update(joining)
+                joining.clear()
                 dirty = True
             if not active:
-                if pending:                                   # idle until the next arrival
+                last_end = None
+                if pending and not waiting:                   # idle until the next arrival
                     self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
                 continue
-            chunk_t0 = self.clock()      # the chunk's wall time covers rebuilds, steps, reads
             if dirty or batch is None:
+                c0 = self.clock()
                 if batch is not None:
                     self.backend.free_batch(batch)
                 batch = self.backend.batch([v[1] for v in active.values()])
                 dirty = False
+                host["batch_s"] += self.clock() - c0
+            if last_end is None:
+                last_end = self.clock()
             n = min(self.chunk, min(v[2] for v in active.values()))
-            ms = self.backend.step(batch, n)
-            for m in ms:
-                step_lat.append((float(m), len(active)))
-                req_step_ms.extend([float(m)] * len(active))
-            work += n * sum(v[0].world.n_cells for v in active.values())
-            resident = len(active)
-            done = [rid for rid, v in active.items() if v[2] - n <= 0]
-            for v in active.values():
-                v[2] -= n
-            if done:
-                self.backend.free_batch(batch)
-                batch = None
-                for rid in done:
-                    r, h, _, adm, need = active.pop(rid)
-                    res = self.backend.read(h)
-                    self.backend.free(h)
-                    used -= need
-                    completed.append(Completed(rid, r.arrival, adm, self.clock() - t0, r.steps,
-                                               r.world.n_cells, res))
-            req_step_wall.extend([1e3 * (self.clock() - chunk_t0) / n] * (resident * n))
+            if asynchronous:
+                inflight = (self.backend.step_async(batch, n), n, len(active))
+            else:
+                inflight = (self.backend.step(batch, n), n, len(active))
         if batch is not None:
             self.backend.free_batch(batch)
         makespan = self.clock() - t0
@@ -187,8 +230,9 @@ class WorldServer:
             "cell_updates_per_s": work / makespan if makespan > 0 else 0.0,
             # device time of the batched step each request-step ran in
             "p50_step_device_ms": float(np.percentile(lat, 50)), "p99_step_device_ms": float(np.percentile(lat, 99)),
-            # wall time per step of the chunk each request-step ran in: batch rebuilds on admission
-            # and completion, the steps, and the read-back of finished worlds included
+            # wall time per step between the ends of consecutive chunks, as each request-step saw
+            # it: batch rebuilds on admission and completion, the steps and the read-back of
+            # finished worlds included
             "p50_step_wall_ms": float(np.percentile(wall, 50)), "p99_step_wall_ms": float(np.percentile(wall, 99)),
             "p50_request_ms_per_step": float(np.percentile(per_req, 50)),
             "p99_request_ms_per_step": float(np.percentile(per_req, 99)),
@@ -197,6 +241,7 @@ class WorldServer:
             "p50_queue_s": float(np.percentile([c.admitted - c.arrival for c in served], 50)) if served else 0.0,
             "p99_queue_s": float(np.percentile([c.admitted - c.arrival for c in served], 99)) if served else 0.0,
             "peak_resident_bytes": peak_used, "budget_bytes": self.budget, "max_worlds": self.max_worlds,
+            "host_s": host,
         }
         return completed, report
 

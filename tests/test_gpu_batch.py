@@ -122,3 +122,89 @@ def test_batched_worlds_match_oracle():
     finally:
         for s in subs:
             s.close()
+
+
+def radiating_worlds(seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k, every in enumerate([2, 0, 3, 1, 2]):
+        W = int(rng.integers(20, 200))
+        H = int(rng.integers(12, 120))
+        out.append(worlds.make_world(width=W, height=H, n_genomes=int(rng.integers(2, 20)), hidden=32, net="cppn",
+                                     seed=300 + k, radiation_every=every, p_mut=6e-3, p_merge=6e-3,
+                                     capacity=400, random_rotation=bool(k % 2)))
+    return out
+
+
+def test_batched_radiation_equals_alone_bit_exact():
+    """Worlds with their own radiation schedules (every 1, 2, 3 steps, or none) inside one batch,
+    over several epochs and two step calls: state, genome tables and stats as stepping alone; the
+    tuner in between (graphs only) leaves the genome tables as they are."""
+    ws = radiating_worlds()
+    alone = []
+    for w in ws:
+        with coral.substrate_for_world(w, coral.BF16_GROUPED) as s:
+            s.step(7)
+            alone.append((s.read_channels(), s.read_genomes(), s.read_stats(0, 7)))
+    subs = [coral.substrate_for_world(w, coral.BF16_GROUPED) for w in ws]
+    try:
+        with coral.Batch(subs) as b:
+            b.step(3)
+            b.tune(trial_steps=1)
+            b.step(4)
+        born = 0
+        for (ref, (genes, parent), stats), s in zip(alone, subs):
+            got = s.read_channels()
+            for k in ref:
+                assert np.array_equal(ref[k], got[k]), k
+            g2, p2 = s.read_genomes()
+            assert np.array_equal(genes, g2) and np.array_equal(parent, p2)
+            bs = s.read_stats(0, 7)
+            for a, c in zip(stats, bs):
+                for k in ("n_mut", "n_merge", "n_born", "n_skipped", "n_live", "n_explore"):
+                    assert a[k] == c[k], (k, a, c)
+            born += sum(a["n_born"] for a in stats)
+        assert born > 0
+    finally:
+        for s in subs:
+            s.close()
+
+
+def test_batched_radiation_matches_oracle():
+    """Exploration off keeps G fixed through the physics, so each radiation event of a batched
+    world sees the same G as the oracle's: hit set, slots, parents and G bit-exact, genes within
+    FP32 rounding, event counts equal; a world without radiation runs alongside."""
+    from oracle import coral_oracle as O
+    from parity import oracle_setup
+    ws = [worlds.make_world(width=96, height=64, n_genomes=10, hidden=32, net="cppn", seed=21, radiation_every=1,
+                            p_mut=4e-3, p_merge=8e-3, capacity=200),
+          worlds.make_world(width=51, height=37, n_genomes=6, hidden=32, net="cppn", seed=22, radiation_every=1,
+                            p_mut=1e-2, p_merge=1e-2, capacity=120, random_rotation=True),
+          worlds.make_world(width=40, height=30, n_genomes=4, hidden=32, net="cppn", seed=23)]
+    for w in ws[:2]:
+        w.physics["k_exp"] = 0.0
+    subs = [coral.substrate_for_world(w, coral.BF16_GROUPED) for w in ws]
+    try:
+        refs = []
+        for w in ws[:2]:
+            st, nets, gen, p = oracle_setup(w)
+            refs.append([st, gen, p])
+        with coral.Batch(subs) as b:
+            for t in range(3):
+                b.step(1)
+                for ref, s in zip(refs, subs[:2]):
+                    st, gen, p = ref
+                    st, gen, slots, ev = O.radiation(st, gen, t, p)
+                    ref[0], ref[1] = st, gen
+                    G = s.read_channels(coral.CH_G)["G"].ravel()
+                    genes, parent = s.read_genomes()
+                    c = s.read_stats(t, 1)[0]
+                    assert np.array_equal(G, st.G), t
+                    assert np.array_equal(parent, gen.parent), t
+                    assert np.max(np.abs(genes - gen.genes)) <= 1e-6 * max(1.0, np.max(np.abs(gen.genes)))
+                    assert c["n_mut"] == ev["n_mut"] and c["n_merge"] == ev["n_merge"]
+                    assert c["n_born"] == ev["n_assigned"] and c["n_skipped"] == ev["n_skipped"]
+        assert sum(r[1].parent[r[1].parent >= 0].size for r in refs) > 0
+    finally:
+        for s in subs:
+            s.close()

@@ -133,3 +133,53 @@ def test_tree_voronoi_equals_plain_voronoi():
         a = worlds._torus_voronoi(W, H, n, np.random.default_rng(seed))
         b = worlds._torus_voronoi_tree(W, H, n, np.random.default_rng(seed))
         assert np.array_equal(a, b)
+
+
+class AsyncFakeBackend(FakeBackend):
+    """step_async on a real worker thread; the step's world set is captured at submission, and
+    worlds created while it runs must not be stepped by it."""
+
+    def __init__(self, clock):
+        super().__init__(clock)
+        from concurrent.futures import ThreadPoolExecutor
+        self.pool = ThreadPoolExecutor(max_workers=1)
+        self.created_during = 0
+        self.running = False
+
+    def create(self, world):
+        if self.running:
+            self.created_during += 1
+        return super().create(world)
+
+    def step_async(self, batch, n):
+        self.running = True
+        members = list(batch)
+
+        def run():
+            for h in members:
+                self.steps[h.name] += n
+            return np.full(n, 1.0 * len(members), np.float32)
+
+        fut = self.pool.submit(run)
+        self.clock.t += 1e-3 * n * len(members)
+
+        class Done:
+            def result(inner):
+                out = fut.result()
+                self.running = False
+                return out
+        return Done()
+
+
+def test_overlapped_stepping_creates_next_worlds_during_a_chunk():
+    clock = FakeClock()
+    be = AsyncFakeBackend(clock)
+    reqs = [serving.Request(0.0005 * k, k, small(k), steps=6 + 5 * k) for k in range(8)]
+    srv = serving.WorldServer(be, budget_bytes=10**12, chunk_steps=3, clock=clock, sleep=clock.sleep)
+    done, rep = srv.run(reqs)
+    assert rep["served"] == 8 and be.live == 0
+    for c in done:
+        assert c.result["steps"] == reqs[c.rid].steps, (c.rid, c.result)
+    assert be.created_during > 0
+    assert rep["cell_updates"] == sum(r.steps * r.world.n_cells for r in reqs)
+    assert set(rep["host_s"]) == {"create_s", "batch_s", "read_free_s", "wait_s"}
