@@ -23,6 +23,11 @@
  *    Channel planes are float32 row-major [height][width]; C is [4][height][width].
  *  - `*_on_device` flags: nonzero = the pointer is a CUDA device pointer on the substrate's
  *    device (for example a torch tensor's data_ptr()), zero = host memory (pinned or pageable).
+ *  - Threads: calls on different substrates and batches may run concurrently from different
+ *    host threads (they share no mutable state; error messages are per handle, or per thread
+ *    for calls without one). Calls on one handle, and on a batch and the substrates it holds,
+ *    must not overlap. coral_bucket_noalloc is the exception: its calls share one scratch
+ *    array and must not overlap at all (see there).
  */
 #ifndef CORAL_H
 #define CORAL_H

@@ -149,6 +149,45 @@ StepArgs step_args(const coral_substrate* s) {
   return a;
 }
 
+// Pageable host memory (not pinned, not registered): a 2-D copy to or from it goes row by row
+// through the driver's staging buffers, so the planes are copied as one contiguous block and
+// re-pitched on the device instead.
+bool pageable(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type == cudaMemoryTypeUnregistered;
+}
+
+// The spare state buffer (the one the next step writes in full) serves as the packed staging
+// area between steps: its E plane holds N >= W * H floats. Afterwards its row padding is set
+// back to zero (the padding of every float plane is zero; the totals sum over pitched rows).
+cudaError_t host_to_pitched(coral_substrate* s, void* dst, const void* src, size_t es) {
+  const size_t W = (size_t)s->W, H = (size_t)s->H, P = (size_t)s->P;
+  float* spare = s->st[s->cur ^ 1].E;
+  cudaError_t e = cudaMemcpyAsync(spare, src, es * W * H, cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(dst, es * P, spare, es * W, es * W, H, cudaMemcpyDeviceToDevice, s->stream);
+  return e;
+}
+
+cudaError_t pitched_to_host(coral_substrate* s, void* dst, const void* src, size_t es) {
+  const size_t W = (size_t)s->W, H = (size_t)s->H, P = (size_t)s->P;
+  float* spare = s->st[s->cur ^ 1].E;
+  cudaError_t e = cudaMemcpy2DAsync(spare, es * W, src, es * P, es * W, H, cudaMemcpyDeviceToDevice, s->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dst, spare, es * W * H, cudaMemcpyDeviceToHost, s->stream);
+  return e;
+}
+
+cudaError_t restore_spare_padding(coral_substrate* s) {
+  const size_t W = (size_t)s->W, H = (size_t)s->H, P = (size_t)s->P;
+  float* spare = s->st[s->cur ^ 1].E;
+  // the staging area is the E plane's first W * H floats: zero them where they cover padding
+  return cudaMemset2DAsync(spare + W, 4 * P, 0, 4 * (P - W), H, s->stream);
+}
+
 cudaMemcpyKind kind_in(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; }
 cudaMemcpyKind kind_out(int on_device) { return on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost; }
 
@@ -332,13 +371,25 @@ int coral_state_load(coral_substrate* s, const float* E, const float* I, const f
   if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
   const Planes& d = s->st[s->cur];
   const cudaMemcpyKind k = kind_in(src_on_device);
-  const size_t W = (size_t)s->W, H = (size_t)s->H, P = (size_t)s->P;
+  const size_t W = (size_t)s->W, H = (size_t)s->H, P = (size_t)s->P, NP = (size_t)s->N;
   // packed rows of W cells in, pitched rows of P cells on the device (the padding untouched)
-  if (E) CK(s, cudaMemcpy2DAsync(d.E, 4 * P, E, 4 * W, 4 * W, H, k, s->stream));
-  if (I) CK(s, cudaMemcpy2DAsync(d.I, 4 * P, I, 4 * W, 4 * W, H, k, s->stream));
-  if (C) CK(s, cudaMemcpy2DAsync(d.C, 4 * P, C, 4 * W, 4 * W, 4 * H, k, s->stream));
-  if (G) CK(s, cudaMemcpy2DAsync(d.G, 4 * P, G, 4 * W, 4 * W, H, k, s->stream));
-  if (R) CK(s, cudaMemcpy2DAsync(d.R, P, R, W, W, H, k, s->stream));
+  const bool stage = !src_on_device && P != W &&
+                     (pageable(E) || pageable(I) || pageable(C) || pageable(G) || pageable(R));
+  auto plane_in = [&](void* dst, const void* src, size_t es) -> int {
+    if (!src) return CORAL_OK;
+    if (stage) {
+      CK(s, host_to_pitched(s, dst, src, es));
+    } else {
+      CK(s, cudaMemcpy2DAsync(dst, es * P, src, es * W, es * W, H, k, s->stream));
+    }
+    return CORAL_OK;
+  };
+  int rc;
+  if ((rc = plane_in(d.E, E, 4)) || (rc = plane_in(d.I, I, 4))) return rc;
+  for (size_t c = 0; c < 4 && C; ++c)
+    if ((rc = plane_in(d.C + c * NP, C + c * W * H, 4))) return rc;
+  if ((rc = plane_in(d.G, G, 4)) || (rc = plane_in(d.R, R, 1))) return rc;
+  if (stage) CK(s, restore_spare_padding(s));
   if (G || R)
     CK(s, launch_validate_state(G ? d.G : nullptr, R ? d.R : nullptr, s->W, s->H, s->P, s->cap, s->status, s->stream));
   // host sources may be pinned: the copies must finish before the caller regains the buffers
@@ -597,12 +648,18 @@ int coral_read_channels(coral_substrate* s, uint32_t mask, void* dst, size_t dst
   char* o = static_cast<char*>(dst);
   const void* src[8] = {d.E, d.I, d.C, d.C + NP, d.C + 2 * NP, d.C + 3 * NP, d.G, d.R};
   const size_t W = (size_t)s->W, H = (size_t)s->H, P = (size_t)s->P;
+  const bool stage = !on_device && P != W && pageable(dst);
   for (int b = 0; b < 8; ++b) {
     if (!(mask & (1u << b))) continue;
     const size_t es = (b == 7) ? 1 : 4;             // pitched rows on the device, packed rows out
-    CK(s, cudaMemcpy2DAsync(o, es * W, src[b], es * P, es * W, H, k, s->stream));
+    if (stage) {
+      CK(s, pitched_to_host(s, o, src[b], es));
+    } else {
+      CK(s, cudaMemcpy2DAsync(o, es * W, src[b], es * P, es * W, H, k, s->stream));
+    }
     o += es * (size_t)N;
   }
+  if (stage) CK(s, restore_spare_padding(s));
   return check_status(s);
 }
 

@@ -112,13 +112,16 @@ class WorldServer:
     def run(self, requests):
         """Serve `requests` (arrival times in seconds from now). Returns (completed, report).
 
-        With a backend that steps asynchronously (``step_async``), the next requests' worlds are
-        admitted and created on the host while the current chunk of steps runs on the device;
-        they join the batch when the chunk ends."""
+        With a backend that steps asynchronously (``step_async``), the host work overlaps the
+        device's chunk of steps: the next requests' worlds are admitted and created (until the
+        chunk ends; they join the batch at the next rebuild), and the worlds that finished with
+        the last chunk are read back (their memory is released at the next chunk end)."""
         pending = sorted(requests)
         waiting = []                     # arrived, not admitted (FIFO by arrival)
         active = {}                      # rid -> [request, handle, remaining, admitted_at, bytes]: in the batch
         joining = {}                     # admitted and created, joining at the next rebuild
+        finished = []                    # left the batch, results not read yet
+        to_free = []                     # read, released when the device is idle
         used = 0
         batch = None
         dirty = False
@@ -132,9 +135,12 @@ class WorldServer:
         inflight = None                  # (future or result, steps, resident worlds)
         last_end = None                  # wall clock at the end of the last chunk
         asynchronous = hasattr(self.backend, "step_async")
-        host = {"create_s": 0.0, "batch_s": 0.0, "read_free_s": 0.0, "wait_s": 0.0}
+        host = {"create_s": 0.0, "batch_s": 0.0, "read_s": 0.0, "free_s": 0.0, "wait_s": 0.0}
 
-        def admit():
+        def chunk_running():
+            return asynchronous and inflight is not None and not inflight[0].done()
+
+        def admit(during_chunk=False):
             nonlocal used, peak_used
             now = self.clock() - t0
             while pending and pending[0].arrival <= now:
@@ -143,8 +149,9 @@ class WorldServer:
                 for r in waiting[:self.prefetch]:
                     self.backend.prepare(r.world)
             # arrival order, while the budget and the slots allow (a request that can never fit
-            # on its own is rejected rather than blocking the queue)
-            while waiting:
+            # on its own is rejected rather than blocking the queue); during a chunk only until
+            # it ends, so that the device does not wait for a burst of admissions
+            while waiting and not (during_chunk and not chunk_running()):
                 r = waiting[0]
                 need = world_bytes(r.world.n_cells, r.world.capacity, r.world.hidden)
                 if need > self.budget:
@@ -161,9 +168,28 @@ class WorldServer:
                 used += need
                 peak_used = max(peak_used, used)
 
-        while pending or waiting or active or joining or inflight:
-            admit()
-            if inflight is not None:                          # the chunk ends
+        def read_finished():
+            c0 = self.clock()
+            for rid, (r, h, _, adm, need) in finished:
+                res = self.backend.read(h)
+                completed.append(Completed(rid, r.arrival, adm, self.clock() - t0, r.steps, r.world.n_cells, res))
+                to_free.append((h, need))
+            finished.clear()
+            host["read_s"] += self.clock() - c0
+
+        def release():
+            nonlocal used
+            c0 = self.clock()
+            for h, need in to_free:
+                self.backend.free(h)
+                used -= need
+            to_free.clear()
+            host["free_s"] += self.clock() - c0
+
+        while pending or waiting or active or joining or inflight or finished or to_free:
+            if inflight is not None:
+                read_finished()                               # overlaps the chunk
+                admit(during_chunk=True)
                 fut, n, resident = inflight
                 c0 = self.clock()
                 ms = fut.result() if asynchronous else fut
@@ -176,27 +202,28 @@ class WorldServer:
                 done = [rid for rid, v in active.items() if v[2] - n <= 0]
                 for v in active.values():
                     v[2] -= n
+                for rid in done:
+                    finished.append((rid, active.pop(rid)))
                 if done:
-                    c0 = self.clock()
-                    self.backend.free_batch(batch)
-                    batch = None
-                    for rid in done:
-                        r, h, _, adm, need = active.pop(rid)
-                        res = self.backend.read(h)
-                        self.backend.free(h)
-                        used -= need
-                        completed.append(Completed(rid, r.arrival, adm, self.clock() - t0, r.steps,
-                                                   r.world.n_cells, res))
-                    host["read_free_s"] += self.clock() - c0
+                    dirty = True
                 end = self.clock()
                 req_step_wall.extend([1e3 * (end - last_end) / n] * (resident * n))
                 last_end = end
-                admit()                                       # freed memory and slots
+            release()                                         # the device is idle here
+            if not asynchronous:
+                read_finished()
+                release()
+            admit()
             if joining:
                 active.update(joining)
                 joining.clear()
                 dirty = True
             if not active:
+                read_finished()
+                release()
+                if batch is not None:
+                    self.backend.free_batch(batch)
+                    batch = None
                 last_end = None
                 if pending and not waiting:                   # idle until the next arrival
                     self.sleep(max(0.0, pending[0].arrival - (self.clock() - t0)))
