@@ -696,17 +696,18 @@ bool encode_sensor_tmap(CUtensorMap* map, const float* E, int W, int H, int P) {
   // rows (pitch P) must be a multiple of 16 bytes; the torus must hold the 40-wide box and 6 rows
   if ((P & 3) != 0 || W < kStageW || H < kHaloH) return false;
   if ((reinterpret_cast<uintptr_t>(E) & 15) != 0) return false;
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // looked up once (a function-local static: thread-safe initialisation)
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !fn) {
       cudaGetLastError();
-      return false;
+      return nullptr;
     }
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return false;
   const cuuint64_t dims[3] = {(cuuint64_t)W, (cuuint64_t)H, 6};
   const cuuint64_t strides[2] = {(cuuint64_t)P * 4, (cuuint64_t)P * (cuuint64_t)H * 4};
   const cuuint32_t box[3] = {(cuuint32_t)kStageW, (cuuint32_t)kHaloH, 6};

@@ -48,7 +48,7 @@ __device__ void block_partial(const double (&s)[NS], const long long (&c)[NC], P
 
 // One thread per cell: gather the rotation-ordered 3x3 neighbourhood of the six sensor
 // channels straight from the SoA planes, run the FP32 net with FMA, apply the actuators.
-__global__ void __launch_bounds__(kP1Threads) k_pass1_fp32(const StepArgs a) {
+__global__ void __launch_bounds__(kP1Threads, 4) k_pass1_fp32(const StepArgs a) {
   const int W = a.W, H = a.H, P = a.P;
   const long long N = a.N;
   double accC[4] = {0, 0, 0, 0};
