@@ -168,6 +168,19 @@ int coral_cppn_generate_weights(coral_substrate* s, const int32_t* slots_or_null
 int coral_step(coral_substrate* s, int32_t n_steps);
 
 /*
+ * Small-genome path of the BF16 tensor-core network (Section "System Design": each cell runs
+ * the net its GenomeIndex selects). A 128-cell tile whose cells hold several genomes runs one
+ * tensor-core round per genome; with cells > 0, a later round whose genome owns at most `cells`
+ * cells of the tile runs on the CUDA cores instead: each of those cells' warps evaluates the
+ * net lane by lane (hidden units spread over the lanes, BF16 operands and FP32 sums as on the
+ * tensor cores, the weights read from the genome's BF16 blob through L1, the ten outputs
+ * reduced over the warp), which saves the tile that round's staging, MMAs and barriers.
+ * 0 (the default) = off. Results equal the tensor-core path's up to the FP32 summation order.
+ * cells in [0, 128], else E_INVALID. No effect on the FP32 path.
+ */
+int coral_set_fma_cutoff(coral_substrate* s, int32_t cells);
+
+/*
  * coral_step with CUDA-event timing (tracing): same work, same stream, plus events recorded
  * around each stage. step_ms: [n_steps] device time of each step; stage_ms: [n_steps][3]
  * time of pass 1 (sense + network + actuators), pass 2 (exploration, flow, day/night) and the
@@ -270,13 +283,18 @@ int coral_batch_step_timed(coral_batch* b, int32_t n_steps, float* step_ms);
  * Autotuner: times trial_steps steps (after one warm-up; graphs only, no radiation, so that
  * the genome tables stay as they are) for each candidate launch shape —
  * pass-1 CTAs per SM in {3, 4, 5, 6} x pass-2 CTAs per SM in {1, 2, 3}, each times 32 as
- * above — keeps the fastest and
+ * above — then, at the fastest shape, the small-genome cutoff (coral_set_fma_cutoff) in
+ * {0, 1, 2, 4, 8}; keeps the fastest and
  * restores every world's state, step index and stats ring afterwards (also after an error,
  * which leaves the launch shape the batch had before the call; a failed save or restore copy
- * returns E_CUDA). choice: [3] = {pass-1 CTAs per SM,
- * pass-2 CTAs per SM, best step time in microseconds} (may be NULL). Synchronises.
+ * returns E_CUDA). choice: [4] = {pass-1 CTAs per SM,
+ * pass-2 CTAs per SM, best step time in microseconds, small-genome cutoff} (may be NULL).
+ * Synchronises.
  */
 int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* choice);
+/* The small-genome cutoff of every world in the batch (as coral_set_fma_cutoff; the batch's
+ * own setting, not the substrates'), until the next tune. Recaptures the batch's graphs. */
+int coral_batch_set_fma_cutoff(coral_batch* b, int32_t cells);
 
 /*
  * Failure-detection self-test (library infrastructure; the paper has no counterpart): launches

@@ -66,6 +66,8 @@ SIGNATURES = {
     "coral_genome_table_load": (ctypes.c_int, [_VP, _I32, _VP, _VP, ctypes.c_int]),
     "coral_cppn_generate_weights": (ctypes.c_int, [_VP, _VP, _I32]),
     "coral_step": (ctypes.c_int, [_VP, _I32]),
+    "coral_set_fma_cutoff": (ctypes.c_int, [_VP, _I32]),
+    "coral_batch_set_fma_cutoff": (ctypes.c_int, [_VP, _I32]),
     "coral_step_timed": (ctypes.c_int, [_VP, _I32, _VP, _VP]),
     "coral_step_jobs": (ctypes.c_int, [_VP, _I32, _VP, _VP, _I32, _I64]),
     "coral_read_channels": (ctypes.c_int, [_VP, _U32, _VP, _SZ, ctypes.c_int]),
@@ -277,6 +279,11 @@ class Substrate:
     def set_step(self, t):
         _check(lib().coral_set_step(self.h, int(t)), self.h)
 
+    def set_fma_cutoff(self, cells):
+        """Small-genome path of the BF16 network: later genome rounds of a tile with at most
+        ``cells`` cells of their genome run on the CUDA cores (0 = off)."""
+        _check(lib().coral_set_fma_cutoff(self.h, int(cells)), self.h)
+
     def get_step(self):
         t = ctypes.c_int64()
         _check(lib().coral_get_step(self.h, ctypes.byref(t)), self.h)
@@ -449,10 +456,14 @@ class Batch:
         self._check(lib().coral_batch_step_timed(self.h, int(n), ms.ctypes.data))
         return ms
 
+    def set_fma_cutoff(self, cells):
+        self._check(lib().coral_batch_set_fma_cutoff(self.h, int(cells)))
+
     def tune(self, trial_steps=3):
-        c = np.zeros(3, np.int32)
+        c = np.zeros(4, np.int32)
         self._check(lib().coral_batch_tune(self.h, int(trial_steps), c.ctypes.data))
-        return {"pass1_ctas_per_sm": int(c[0]), "pass2_ctas_per_sm": int(c[1]), "step_us": int(c[2])}
+        return {"pass1_ctas_per_sm": int(c[0]), "pass2_ctas_per_sm": int(c[1]), "step_us": int(c[2]),
+                "fma_cutoff": int(c[3])}
 
     def close(self):
         if getattr(self, "h", None):

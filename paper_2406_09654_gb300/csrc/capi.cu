@@ -62,6 +62,7 @@ struct coral_substrate {
   int32_t* sort_buf = nullptr;
   long long t = 0;
   int grid1 = 0, grid2 = 0;
+  int fma_cutoff = 0;           // BF16 pass 1: FMA path for later genome rounds of at most this many cells
   JobPipe jobs;
   // row slab of a larger world (coral_slab_set): own rows [row_lo, row_hi), global id of the
   // first own cell; radiation then runs through coral_slab_radiation_scan / _apply
@@ -146,6 +147,7 @@ StepArgs step_args(const coral_substrate* s) {
   a.capacity = s->cap;
   a.step_dev = nullptr;
   a.sched = s->sched;
+  a.fma_cutoff = s->fma_cutoff;
   return a;
 }
 
@@ -363,6 +365,13 @@ int coral_substrate_destroy(coral_substrate* s) {
       if (ev) cudaEventDestroy(ev);
   free_all(s);
   delete s;
+  return CORAL_OK;
+}
+
+int coral_set_fma_cutoff(coral_substrate* s, int32_t cells) {
+  if (!s) return fail(nullptr, CORAL_E_INVALID, "NULL substrate");
+  if (cells < 0 || cells > kFmaCutoffMax) return fail(s, CORAL_E_INVALID, "cells must be in [0, 128]");
+  s->fma_cutoff = cells;
   return CORAL_OK;
 }
 
@@ -992,6 +1001,7 @@ struct coral_batch {
   CUtensorMap* d_tmaps = nullptr;  // [2][n]
   int* d_tma_ok = nullptr;         // [n]
   int cps1 = 6, cps2 = 3;        // CTAs per SM of pass 1 / pass 2
+  int fma_cutoff = 0;            // pass 1's FMA small-genome cutoff for every world of the batch
   int grid1 = 0, grid2 = 0;
   int max_grid = 0;
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -1102,7 +1112,7 @@ int batch_configure(coral_batch* b) {
     }
     cudaGraph_t graph = nullptr;
     BCK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = launch_pass1_bf16_batch(t, p, b->grid1, b->worlds[0]->p.hidden, b->stream);
+    cudaError_t e = launch_pass1_bf16_batch(t, p, b->grid1, b->worlds[0]->p.hidden, b->fma_cutoff > 0, b->stream);
     if (e == cudaSuccess) e = launch_pass2_batch(t, p, b->grid2, b->stream);
     if (e == cudaSuccess) e = launch_stats_batch(t, b->stream);
     const cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
@@ -1155,6 +1165,7 @@ int batch_upload_args(coral_batch* b) {
       StepArgs a = step_args(s);
       s->cur = save;
       a.step_dev = b->d_steps + i;
+      a.fma_cutoff = b->fma_cutoff;
       args[(size_t)p * b->n + i] = a;
       if (s->tmap_ok) maps[(size_t)p * b->n + i] = s->tmap[save ^ p];
       else memset(&maps[(size_t)p * b->n + i], 0, sizeof(CUtensorMap));
@@ -1292,6 +1303,16 @@ int batch_run(coral_batch* b, int32_t n_steps, float* step_ms, bool radiation = 
 
 extern "C" int coral_batch_step(coral_batch* b, int32_t n_steps) { return batch_run(b, n_steps, nullptr); }
 
+extern "C" int coral_batch_set_fma_cutoff(coral_batch* b, int32_t cells) {
+  if (!b) return bfail(nullptr, CORAL_E_INVALID, "NULL batch");
+  if (cells < 0 || cells > kFmaCutoffMax) return bfail(b, CORAL_E_INVALID, "cells must be in [0, 128]");
+  const int old = b->fma_cutoff;
+  b->fma_cutoff = cells;
+  const int rc = batch_configure(b);                  // the graphs launch the matching kernel
+  if (rc != CORAL_OK) b->fma_cutoff = old;
+  return rc;
+}
+
 extern "C" int coral_batch_step_timed(coral_batch* b, int32_t n_steps, float* step_ms) {
   if (!step_ms) return bfail(b, CORAL_E_INVALID, "step_ms is NULL");
   return batch_run(b, n_steps, step_ms);
@@ -1348,6 +1369,27 @@ extern "C" int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* ch
         b2 = c2s[i2];
       }
     }
+  // the FMA small-genome cutoff at the chosen launch shape (the shapes are timed without it)
+  const int fma_0 = b->fma_cutoff;
+  int bf = fma_0;
+  if (rc == CORAL_OK) {
+    const int cuts[5] = {0, 1, 2, 4, 8};
+    float best_f = 1e30f;
+    b->cps1 = b1;
+    b->cps2 = b2;
+    for (int i = 0; i < 5 && rc == CORAL_OK; ++i) {
+      b->fma_cutoff = cuts[i];
+      if ((rc = batch_configure(b)) != CORAL_OK) break;
+      if ((rc = batch_run(b, trial_steps + 1, ms.data(), false)) != CORAL_OK) break;
+      float tot = 0;
+      for (int k = 1; k <= trial_steps; ++k) tot += ms[k];
+      if (tot < best_f) {
+        best_f = tot;
+        bf = cuts[i];
+      }
+    }
+    if (rc == CORAL_OK) best = best_f;
+  }
   // restore the states, step indices and stats rings, also after an error
   cudaError_t e = cudaStreamSynchronize(b->stream);
   for (int i = 0; i < b->n; ++i) {
@@ -1370,6 +1412,7 @@ extern "C" int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* ch
     // back to the launch shape the batch had before tuning
     b->cps1 = cps1_0;
     b->cps2 = cps2_0;
+    b->fma_cutoff = fma_0;
     const std::string keep = b->err;
     batch_configure(b);
     b->err = keep;
@@ -1378,11 +1421,13 @@ extern "C" int coral_batch_tune(coral_batch* b, int32_t trial_steps, int32_t* ch
   }
   b->cps1 = b1;
   b->cps2 = b2;
+  b->fma_cutoff = bf;
   if ((rc = batch_configure(b)) != CORAL_OK) return rc;
   if (choice) {
     choice[0] = b1;
     choice[1] = b2;
     choice[2] = (int32_t)(1000.0f * best / trial_steps);
+    choice[3] = bf;
   }
   return CORAL_OK;
 }

@@ -87,6 +87,8 @@ struct Partial {   // per-block partial sums of one step (FP64), fixed-order com
 // part of the torus (G = -1, R = 0, floats 0). N = H * P is the plane length.
 __host__ __device__ inline int row_pitch(int W) { return (W + 3) & ~3; }
 
+constexpr int kFmaCutoffMax = 128;   // the FMA small-genome cutoff: at most a whole tile
+
 struct __align__(8) StepArgs {
   int W, H;
   long long N;                  // H * P
@@ -111,6 +113,8 @@ struct __align__(8) StepArgs {
                                // is taken from it); NULL: use is_day
   int* sched;                  // BF16 pass 1's tile pool: [0] next chunk, [1] CTAs done (both 0
                                // between launches: the last CTA of a launch resets them)
+  int fma_cutoff;              // BF16 pass 1: a later genome round of a tile with at most this many
+                               // cells runs on the warp-level FMA path (0: never)
 };
 
 // Batched stepping of many worlds (same hidden size, BF16 path): the CTAs of each launch are
@@ -215,7 +219,8 @@ __device__ __forceinline__ void copy_args_to_shared(StepArgs* dst, const StepArg
 }
 
 cudaError_t prepare_pass1_bf16_batch();   // kernel attributes, once before any capture
-cudaError_t launch_pass1_bf16_batch(const BatchTable& b, int parity, int grid, int hidden, cudaStream_t st);
+cudaError_t launch_pass1_bf16_batch(const BatchTable& b, int parity, int grid, int hidden, bool fma,
+                                    cudaStream_t st);
 cudaError_t launch_pass2_batch(const BatchTable& b, int parity, int grid, cudaStream_t st);
 cudaError_t launch_stats_batch(const BatchTable& b, cudaStream_t st);
 int pass1_fp32_grid(int sms);

@@ -124,11 +124,96 @@ __device__ __forceinline__ void issue_halo(const StepArgs& a, int x0, int y0, ui
   tc::cp_async_commit();
 }
 
+// Warp-level FMA evaluation of one genome's net for the rows of this warp given in `rows`
+// (the small-genome path): for each such row in turn, the 32 lanes compute the hidden units
+// lane and lane + 32 from the row's BF16 input (shared memory, the MMA's input tile) and the
+// genome's BF16 blob (global memory: W1 rows, W2 rows, b2, the layout the MMA reads), with the
+// MMA path's arithmetic: BF16 operands, FP32 sums, tanh.approx hidden values rounded to BF16;
+// the ten layer-2 sums are reduced over the warp. Returns this lane's row outputs (before the
+// output tanh, b2 added) in zo when its row is in `rows`.
+template <int H>
+__device__ __forceinline__ void fma_round(unsigned rows, uint32_t tile_s, const uint8_t* blob, int warp, int lane,
+                                          float (&zo)[kOut]) {
+  constexpr int N1 = H ? H : 16;
+  while (rows) {
+    const int lr = __ffs(rows) - 1;
+    rows &= rows - 1;
+    const int row = warp * 32 + lr;
+    const uint32_t xrow = tile_s + (uint32_t)row * 128u;
+    // output (H = 0) or hidden units u0 = lane, u1 = lane + 32 of layer 1
+    const int u0 = lane, u1 = lane + 32;
+    const bool has0 = u0 < (H ? H : kOut), has1 = H > 32 && u1 < H;
+    float acc0 = 0.0f, acc1 = 0.0f;
+#pragma unroll 1
+    for (int p = 0; p < 8; ++p) {                     // not unrolled: few registers on this rare path
+      uint32_t xw[4];
+      asm volatile("ld.shared.v4.b32 {%0,%1,%2,%3}, [%4];"
+                   : "=r"(xw[0]), "=r"(xw[1]), "=r"(xw[2]), "=r"(xw[3])
+                   : "r"(xrow + ((((uint32_t)p ^ (uint32_t)row) & 7u) << 4)));
+      float x[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        x[2 * i] = __uint_as_float(xw[i] << 16);
+        x[2 * i + 1] = __uint_as_float(xw[i] & 0xFFFF0000u);
+      }
+      if (has0) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(blob + u0 * 128 + (((p ^ u0) & 7) << 4)));
+        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          acc0 = fmaf(x[2 * i], __uint_as_float(ww[i] << 16), acc0);
+          acc0 = fmaf(x[2 * i + 1], __uint_as_float(ww[i] & 0xFFFF0000u), acc0);
+        }
+      }
+      if (has1) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(blob + u1 * 128 + (((p ^ u1) & 7) << 4)));
+        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          acc1 = fmaf(x[2 * i], __uint_as_float(ww[i] << 16), acc1);
+          acc1 = fmaf(x[2 * i + 1], __uint_as_float(ww[i] & 0xFFFF0000u), acc1);
+        }
+      }
+    }
+    if constexpr (H == 0) {
+#pragma unroll
+      for (int o = 0; o < kOut; ++o) {
+        const float z = __shfl_sync(0xffffffffu, acc0, o);
+        if (lane == lr) zo[o] = z;
+      }
+    } else {
+      // hidden values as the MMA's A operand holds them: tanh, rounded to BF16
+      const float h0 = has0 ? __uint_as_float(tc::pack_bf16x2(0.0f, tc::tanh_approx(acc0)) & 0xFFFF0000u) : 0.0f;
+      const float h1 = has1 ? __uint_as_float(tc::pack_bf16x2(0.0f, tc::tanh_approx(acc1)) & 0xFFFF0000u) : 0.0f;
+      const uint8_t* w2 = blob + N1 * 128;
+#pragma unroll
+      for (int o = 0; o < kOut; ++o) {
+        float part = 0.0f;
+        if (has0) {
+          const uint16_t b = __ldg(reinterpret_cast<const unsigned short*>(
+              w2 + o * 128 + ((((u0 >> 3) ^ o) & 7) << 4) + ((u0 & 7) << 1)));
+          part = h0 * __uint_as_float((uint32_t)b << 16);
+        }
+        if (has1) {
+          const uint16_t b = __ldg(reinterpret_cast<const unsigned short*>(
+              w2 + o * 128 + ((((u1 >> 3) ^ o) & 7) << 4) + ((u1 & 7) << 1)));
+          part = fmaf(h1, __uint_as_float((uint32_t)b << 16), part);
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+        if (lane == lr) zo[o] = part + __ldg(reinterpret_cast<const float*>(w2 + 16 * 128) + o);
+      }
+    }
+  }
+}
+
 // One CTA's share of pass 1 for one world: CTA `cta` of `ncta` takes a contiguous run of tiles,
 // then pool chunks (see kStaticNum); its partial sums go to a.part1[cta]. tmap: TMA descriptor (use_tma != 0) or unused.
 // kH: the hidden size (0 = one layer), a compile-time constant so that the per-chunk loops and
 // the layer-2 branch are resolved by the compiler; one instantiation per supported size.
-template <int kH>
+// kFma: the instantiation with the warp-level FMA path for small genomes (fma_round), used
+// when a.fma_cutoff > 0; the default instantiation has none of its code.
+template <int kH, bool kFma>
 __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtensorMap* tmap, const int use_tma,
                                                 const int cta, const int ncta) {
   extern __shared__ uint8_t smem_raw[];
@@ -392,6 +477,28 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
         const unsigned b = __ballot_sync(0xffffffffu, !done && !mine);   // pending after this round
         if (lane == 0) ballots[4 * (rb ^ 1) + warp] = b;
       }
+      if constexpr (kFma) {
+        // a later round whose genome has at most fma_cutoff rows in the tile: those rows by
+        // warp-level FMA, no tensor-core round (the count's barrier publishes the ballots)
+        if (!first_round) {
+          const int cnt = __syncthreads_count(mine);
+          if (cnt <= a.fma_cutoff) {
+            const int gsafe = (unsigned)gs < (unsigned)a.capacity ? gs : 0;
+            float zo[kOut];
+            fma_round<H>(__ballot_sync(0xffffffffu, mine), a_s, a.nets16 + (long long)gsafe * a.blob_bytes, warp,
+                         lane, zo);
+            if (mine) {
+              float act[kOut];
+#pragma unroll
+              for (int o = 0; o < kOut; ++o) act[o] = tc::tanh_approx(zo[o]);
+              finish(act, zo);
+              done = true;
+            }
+            rb ^= 1;
+            continue;                                 // the next round starts with a CTA barrier
+          }
+        }
+      }
       if constexpr (H == 0) {                         // no hidden-tile barrier: this one publishes
         if (__syncthreads_or(bad)) {                  // the ballots before the next round reads them
           timed_out = true;
@@ -528,13 +635,13 @@ __device__ __forceinline__ void pass1_bf16_body(const StepArgs& a, const CUtenso
   }
 }
 
-template <int kH>
+template <int kH, bool kFma>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm)
     k_pass1_bf16(const __grid_constant__ StepArgs a, const __grid_constant__ CUtensorMap tmap, const int use_tma) {
-  pass1_bf16_body<kH>(a, &tmap, use_tma, blockIdx.x, gridDim.x);
+  pass1_bf16_body<kH, kFma>(a, &tmap, use_tma, blockIdx.x, gridDim.x);
 }
 
-template <int kH>
+template <int kH, bool kFma>
 __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16_batch(const __grid_constant__ BatchTable bt,
                                                                           const int parity) {
   __shared__ StepArgs sa;
@@ -546,7 +653,7 @@ __global__ void __launch_bounds__(kThreads, kCtasPerSm) k_pass1_bf16_batch(const
   const int use_tma = bt.tma_ok[w];
   if (use_tma && threadIdx.x == 0) tc::fence_tensormap_acquire(tm);
   __syncthreads();
-  pass1_bf16_body<kH>(sa, tm, use_tma, blockIdx.x - bt.world_first1[w], bt.world_ctas1[w]);
+  pass1_bf16_body<kH, kFma>(sa, tm, use_tma, blockIdx.x - bt.world_first1[w], bt.world_ctas1[w]);
 }
 
 // A wait that must run out: nothing arrives on the barrier. Same bounded wait, error report
@@ -612,9 +719,15 @@ namespace {
 // the kernel instantiations, indexed by hidden size / 16 (0, 16, 32, 48, 64)
 using P1Fn = void (*)(StepArgs, CUtensorMap, int);
 using P1BFn = void (*)(BatchTable, int);
-const P1Fn kP1[5] = {k_pass1_bf16<0>, k_pass1_bf16<16>, k_pass1_bf16<32>, k_pass1_bf16<48>, k_pass1_bf16<64>};
-const P1BFn kP1B[5] = {k_pass1_bf16_batch<0>, k_pass1_bf16_batch<16>, k_pass1_bf16_batch<32>,
-                       k_pass1_bf16_batch<48>, k_pass1_bf16_batch<64>};
+// [FMA small-genome path off / on][hidden size / 16]
+const P1Fn kP1[2][5] = {{k_pass1_bf16<0, false>, k_pass1_bf16<16, false>, k_pass1_bf16<32, false>,
+                         k_pass1_bf16<48, false>, k_pass1_bf16<64, false>},
+                        {k_pass1_bf16<0, true>, k_pass1_bf16<16, true>, k_pass1_bf16<32, true>,
+                         k_pass1_bf16<48, true>, k_pass1_bf16<64, true>}};
+const P1BFn kP1B[2][5] = {{k_pass1_bf16_batch<0, false>, k_pass1_bf16_batch<16, false>, k_pass1_bf16_batch<32, false>,
+                           k_pass1_bf16_batch<48, false>, k_pass1_bf16_batch<64, false>},
+                          {k_pass1_bf16_batch<0, true>, k_pass1_bf16_batch<16, true>, k_pass1_bf16_batch<32, true>,
+                           k_pass1_bf16_batch<48, true>, k_pass1_bf16_batch<64, true>}};
 int hidden_index(int hidden) { return (hidden >= 0 && hidden <= 64 && hidden % 16 == 0) ? hidden / 16 : -1; }
 }  // namespace
 
@@ -628,8 +741,8 @@ int pass1_bf16_grid(int sms) {
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   if (major != 10) return 0;                                  // tcgen05 needs the sm_100 family
   int per_sm = kCtasPerSm, max_regs = 0, static_smem = 0;
-  for (int k = 0; k < 5; ++k) {
-    const void* fn = reinterpret_cast<const void*>(kP1[k]);
+  for (int k = 0; k < 10; ++k) {
+    const void* fn = reinterpret_cast<const void*>(kP1[k / 5][k % 5]);
     int n = 0;
     cudaFuncAttributes fa;
     if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes) != cudaSuccess ||
@@ -663,8 +776,8 @@ int pass1_bf16_grid(int sms) {
 }
 
 cudaError_t prepare_pass1_bf16_batch() {
-  for (int k = 0; k < 5; ++k) {
-    const void* fn = reinterpret_cast<const void*>(kP1B[k]);
+  for (int k = 0; k < 10; ++k) {
+    const void* fn = reinterpret_cast<const void*>(kP1B[k / 5][k % 5]);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -673,10 +786,11 @@ cudaError_t prepare_pass1_bf16_batch() {
   return cudaSuccess;
 }
 
-cudaError_t launch_pass1_bf16_batch(const BatchTable& b, int parity, int grid, int hidden, cudaStream_t st) {
+cudaError_t launch_pass1_bf16_batch(const BatchTable& b, int parity, int grid, int hidden, bool fma,
+                                    cudaStream_t st) {
   const int k = hidden_index(hidden);
   if (k < 0) return cudaErrorInvalidValue;
-  kP1B[k]<<<grid, kThreads, kSmemBytes, st>>>(b, parity);
+  kP1B[fma ? 1 : 0][k]<<<grid, kThreads, kSmemBytes, st>>>(b, parity);
   return cudaGetLastError();
 }
 
@@ -688,7 +802,7 @@ cudaError_t launch_pass1_bf16(const StepArgs& a, const CUtensorMap* tmap, cudaSt
     m = *tmap;
   else
     memset(&m, 0, sizeof(m));
-  kP1[k]<<<grid, kThreads, kSmemBytes, st>>>(a, m, tmap ? 1 : 0);
+  kP1[a.fma_cutoff > 0 ? 1 : 0][k]<<<grid, kThreads, kSmemBytes, st>>>(a, m, tmap ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -63,6 +63,8 @@ def test_batch_tuner_restores_state_and_mixes_with_single_steps():
         with coral.Batch(subs) as b:
             choice = b.tune(trial_steps=2)
             assert choice["pass1_ctas_per_sm"] in (3, 4, 5, 6) and choice["pass2_ctas_per_sm"] in (1, 2, 3)
+            assert choice["fma_cutoff"] in (0, 1, 2, 4, 8)
+            b.set_fma_cutoff(0)                      # the steps below: the tensor-core path only
             subs[0].step(1)                          # one world steps alone in between
             b.step(2)
         for w, s, extra in zip(ws, subs, [1, 0, 0, 0, 0]):
@@ -205,6 +207,31 @@ def test_batched_radiation_matches_oracle():
                     assert c["n_mut"] == ev["n_mut"] and c["n_merge"] == ev["n_merge"]
                     assert c["n_born"] == ev["n_assigned"] and c["n_skipped"] == ev["n_skipped"]
         assert sum(r[1].parent[r[1].parent >= 0].size for r in refs) > 0
+    finally:
+        for s in subs:
+            s.close()
+
+
+def test_batched_fma_path_equals_alone():
+    """With the small-genome path on (cutoff 8), each batched world is bit-identical to the same
+    world stepped alone with that cutoff (both run the same kernel body)."""
+    ws = [worlds.make_square_world(side, n, 32, seed=side + n) for side, n in ((96, 40), (200, 150), (64, 9))]
+    ws.append(worlds.make_world(width=77, height=50, n_genomes=25, hidden=32, layout="random", net="cppn", seed=3))
+    alone = []
+    for w in ws:
+        with coral.substrate_for_world(w, coral.BF16_GROUPED) as s:
+            s.set_fma_cutoff(8)
+            s.step(4)
+            alone.append(s.read_channels())
+    subs = [coral.substrate_for_world(w, coral.BF16_GROUPED) for w in ws]
+    try:
+        with coral.Batch(subs) as b:
+            b.set_fma_cutoff(8)
+            b.step(4)
+        for ref, s in zip(alone, subs):
+            got = s.read_channels()
+            for k in ref:
+                assert np.array_equal(ref[k], got[k]), k
     finally:
         for s in subs:
             s.close()

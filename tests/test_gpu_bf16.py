@@ -37,7 +37,7 @@ def _lib():
     assert coral.bf16_available(), "the tcgen05 path must be available on this GPU"
 
 
-def forced(world, steps, tol, tau, t0=0, net_precision="fp64", max_band_frac=MAX_BAND, warm=0):
+def forced(world, steps, tol, tau, t0=0, net_precision="fp64", max_band_frac=MAX_BAND, warm=0, fma_cutoff=0):
     """Oracle-forced steps: each step starts from the oracle's state on both sides (after `warm`
     oracle-only steps from t0). Returns the worst per-channel errors, the share of cells in the
     band (over all compared steps) and, for the FP64 contract, the fixed band's breakdown."""
@@ -45,6 +45,7 @@ def forced(world, steps, tol, tau, t0=0, net_precision="fp64", max_band_frac=MAX
     if net_precision == "fp64":
         _, nets_b, _, p_b = oracle_setup(world, net_precision="bf16")
     sub = coral.substrate_for_world(world, coral.BF16_GROUPED)
+    sub.set_fma_cutoff(fma_cutoff)
     worst, band, fixed = {}, 0, []
     try:
         st = round32(st)
@@ -86,8 +87,7 @@ def forced(world, steps, tol, tau, t0=0, net_precision="fp64", max_band_frac=MAX
 @pytest.mark.parametrize("W,H,n,hidden,layout", [(64, 64, 8, 0, "voronoi"), (96, 40, 6, 32, "voronoi"),
                                                  (37, 29, 5, 64, "voronoi"), (33, 7, 3, 16, "voronoi"),
                                                  (64, 64, 9, 48, "voronoi"), (40, 24, 50, 64, "random"),
-                                                 # rows not a multiple of 16 bytes: the halo of interior
-                                                 # tiles comes by cp.async
+                                                 # widths that are not a multiple of 4 (padded rows)
                                                  (130, 70, 10, 64, "voronoi"), (141, 43, 8, 32, "random"),
                                                  (103, 37, 6, 16, "voronoi")])
 def test_bf16_matches_bf16_operand_oracle(W, H, n, hidden, layout):
@@ -142,3 +142,51 @@ def test_bf16_radiation_and_determinism():
         assert np.array_equal(outs[0][k], outs[1][k]), k
     # tiles are shared out dynamically among the CTAs; the totals stay bit-identical
     assert stats[0] == stats[1]
+
+
+OPERAND_WORLDS = [(64, 64, 8, 0, "voronoi"), (96, 40, 6, 32, "voronoi"), (37, 29, 5, 64, "voronoi"),
+                  (33, 7, 3, 16, "voronoi"), (64, 64, 9, 48, "voronoi"), (40, 24, 50, 64, "random"),
+                  (130, 70, 10, 64, "voronoi"), (141, 43, 8, 32, "random"), (103, 37, 6, 16, "voronoi")]
+
+
+@pytest.mark.parametrize("W,H,n,hidden,layout", OPERAND_WORLDS)
+def test_fma_small_genome_path_matches_bf16_operand_oracle(W, H, n, hidden, layout):
+    """The worlds of the test above with cutoff 128: every later genome round of a tile runs on
+    the warp-level FMA path (a tile's first round stays on the tensor cores), with the
+    tensor-core path's operands (BF16 inputs, weights and hidden values, FP32 sums); the same
+    tolerance and band gates."""
+    w = worlds.make_world(width=W, height=H, n_genomes=n, hidden=hidden, layout=layout,
+                          net="cppn" if hidden else "direct", seed=W + H + hidden, random_rotation=True)
+    limit = 0.15 if n == 50 else MAX_BAND
+    worst, frac, _ = forced(w, 3, BF16_OP_TOL, BF16_OP_TAU, t0=98, net_precision="bf16", max_band_frac=limit,
+                            fma_cutoff=128)
+    print(W, H, hidden, layout, "worst", worst, "band fraction", round(frac, 4))
+
+
+def test_fma_cutoff_is_validated():
+    w = worlds.make_world(width=16, height=16, n_genomes=2, hidden=16, net="cppn", seed=1)
+    with coral.substrate_for_world(w, coral.BF16_GROUPED) as sub:
+        for bad in (-1, 129):
+            with pytest.raises(coral.CoralError) as e:
+                sub.set_fma_cutoff(bad)
+            assert e.value.code == coral.E_INVALID
+        sub.set_fma_cutoff(0)
+        sub.set_fma_cutoff(128)
+
+
+def test_fma_path_is_taken_and_close_to_tensor_core_path():
+    """One step of a cell-by-cell random world with the small-genome path off and on: the FMA
+    sums run in another order than the tensor core's, so some outputs differ in their last
+    bits (the path did run), all within the BF16-operand tolerance."""
+    w = worlds.make_world(width=40, height=24, n_genomes=50, hidden=64, layout="random", net="cppn", seed=128)
+    outs = []
+    for cut in (0, 128):
+        with coral.substrate_for_world(w, coral.BF16_GROUPED) as sub:
+            sub.set_step(98)
+            sub.set_fma_cutoff(cut)
+            sub.step(1)
+            outs.append(sub.read_channels())
+    a, b = outs
+    assert any(not np.array_equal(a[k], b[k]) for k in ("C0", "C1", "C2", "C3"))
+    for k in ("C0", "C1", "C2", "C3"):
+        assert np.max(np.abs(a[k] - b[k])) <= BF16_OP_TOL * max(1.0, float(np.max(np.abs(a[k]))))
