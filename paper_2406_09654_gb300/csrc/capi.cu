@@ -697,10 +697,14 @@ int coral_read_perm(coral_substrate* s, int32_t* dst_counts, int32_t* dst_perm) 
     const size_t words = 6 * (size_t)N + 256 * (size_t)nblk + (size_t)s->cap + 256 + 64;
     CK(s, dalloc(s, &s->sort_buf, words));
   }
-  // the torus cells' G packed (cell id y * W + x), then sorted
-  int32_t* keys = s->sort_buf + 5 * (size_t)N + 256 * (size_t)nblk + (size_t)s->cap + 256;
-  CK(s, cudaMemcpy2DAsync(keys, 4 * (size_t)s->W, s->st[s->cur].G, 4 * (size_t)s->P, 4 * (size_t)s->W, (size_t)s->H,
-                          cudaMemcpyDeviceToDevice, s->stream));
+  // the torus cells' G packed (cell id y * W + x), then sorted; unpadded rows are packed already
+  const int32_t* keys = s->st[s->cur].G;
+  if (s->P != s->W) {
+    int32_t* packed = s->sort_buf + 5 * (size_t)N + 256 * (size_t)nblk + (size_t)s->cap + 256;
+    CK(s, cudaMemcpy2DAsync(packed, 4 * (size_t)s->W, s->st[s->cur].G, 4 * (size_t)s->P, 4 * (size_t)s->W,
+                            (size_t)s->H, cudaMemcpyDeviceToDevice, s->stream));
+    keys = packed;
+  }
   SortArgs a = {};
   a.keys_in = keys;
   a.N = N;
