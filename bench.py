@@ -64,6 +64,10 @@ def parse():
     ap.add_argument("--batched-steps", type=int, default=10, help="steps of the 256-world batch (0 = skip)")
     ap.add_argument("--serving-requests", type=int, default=200, help="requests of the serving run (0 = skip)")
     ap.add_argument("--serving-slots", type=int, default=64, help="batch slots of the serving run")
+    ap.add_argument("--batch-worlds", type=int, default=256,
+                    help="--workload cfg4: worlds in the batch (256 = the workload; fewer for profiling "
+                         "a small case)")
+    ap.add_argument("--no-tune", action="store_true", help="--workload cfg4: keep the default launch shape")
     return ap.parse_args()
 
 
@@ -602,14 +606,18 @@ def main():
         build.build()
         barrier(world_size)
         t0 = time.perf_counter()
-        r = run_batched(256, a.steps, a.warmup, seed=rank)
+        r = run_batched(a.batch_worlds, a.steps, a.warmup, seed=rank, tune=not a.no_tune)
         el = max_over_ranks(r["ms_per_step"] * a.steps / 1e3, world_size)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": r["cells"] * a.steps * world_size / el, "unit": "cell-updates/s",
                               "n_gpus": world_size, "steps": a.steps, "warmup": a.warmup,
                               "ms_per_step": 1e3 * el / a.steps, "higher_is_better": True, "scaling": "weak",
                               "vs_baseline": None, "dtype": "bf16 network operands, f32 accumulation and state",
-                              "data": "synthetic", "config": {"workload": f"cfg4: {WORKLOADS['cfg4']}",
+                              "data": "synthetic", "config": {"workload": f"cfg4: {WORKLOADS['cfg4']}"
+                                                              if a.batch_worlds == 256 else
+                                                              f"cfg4 distributions, {a.batch_worlds} worlds "
+                                                              "(a smaller batch, e.g. for profiling)",
+                                                              "worlds": a.batch_worlds,
                                                               "cells": r["cells"], "tuned": r["tuned"]},
                               "p50_step_ms": r["p50_step_ms"], "p99_step_ms": r["p99_step_ms"],
                               "wall_s": time.perf_counter() - t0}))
