@@ -126,7 +126,8 @@ __device__ __forceinline__ void issue_halo(const StepArgs& a, int x0, int y0, ui
 
 // Warp-level FMA evaluation of one genome's net for the rows of this warp given in `rows`
 // (the small-genome path): for each such row in turn, the 32 lanes compute the hidden units
-// lane and lane + 32 from the row's BF16 input (shared memory, the MMA's input tile) and the
+// lane and lane + 32 (with one layer, H = 0: lanes 0..9 the ten outputs) from the row's BF16
+// input (shared memory, the MMA's input tile) and the
 // genome's BF16 blob (global memory: W1 rows, W2 rows, b2, the layout the MMA reads), with the
 // MMA path's arithmetic: BF16 operands, FP32 sums, tanh.approx hidden values rounded to BF16;
 // the ten layer-2 sums are reduced over the warp. Returns this lane's row outputs (before the
